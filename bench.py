@@ -1,0 +1,364 @@
+#!/usr/bin/env python3
+"""Benchmark of the ECC hot path: line-pair samples per second on one GB300.
+
+Workload (default): the 496-view, 200-degree short scan (620x480 detector, 0.6 mm
+pixels, SID 750 / SDD 1200 mm, 40 seeded ellipsoids), 768x768 dRadon/ds grid,
+512 plane angles per pair, all 122,760 view pairs.  One step is the whole path on
+inputs resident in HBM: per-view set-up, the dRadon/ds precompute of every view,
+the pair set-up and the pair x kappa gather-reduce down to the total.  One unit
+is one (pair, kappa) sample with both look-ups.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun with N > 1 every rank runs its own
+independent copy of the workload (weak scaling; no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "ECC line-pair samples/s"
+UNIT = "line-pair samples/s"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+FLOPS_PER_TAP = 4                                    # lerp (sub + fma) + accumulate
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="c2", choices=["c2"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def workload_config(cfg):
+    return {
+        "workload": (f"{cfg.name}: {cfg.n_views}-view {cfg.arc_deg:g}-degree short scan, {cfg.W}x{cfg.H} detector "
+                     f"({cfg.pixel_mm} mm), {cfg.n_prim} seeded ellipsoids, {cfg.n_alpha}x{cfg.n_s} dRadon/ds, "
+                     f"{cfg.K} kappa, all {cfg.n_pairs} pairs; step = dRadon/ds precompute + ECC evaluation"),
+        "n_views": cfg.n_views, "n_pairs": cfg.n_pairs, "n_kappa": cfg.K, "n_alpha": cfg.n_alpha, "n_s": cfg.n_s,
+        "detector": [cfg.W, cfg.H],
+        "l2": "inputs larger than L2 (projections 590 MB, sinograms 1.17 GB > 135 MB L2); no flush",
+        "parallelism": "independent replicas per GPU",
+    }
+
+
+def joseph_taps(cfg) -> int:
+    """Taps of the Joseph line sums that fall inside the image (algorithmic work of
+    the dRadon/ds precompute): per line, the integer steps where the interpolation
+    coordinate lies in (-1, limit)."""
+    W, H, n_alpha, n_s = cfg.W, cfg.H, cfg.n_alpha, cfg.n_s
+    ds = np.hypot(W, H) / (n_s - 1)
+    cx, cy = 0.5 * (W - 1), 0.5 * (H - 1)
+    m = np.arange(n_alpha)
+    a = m * np.pi / n_alpha
+    ca, sa = np.cos(a), np.sin(a)
+    rows = (4 * m <= n_alpha) | (4 * m >= 3 * n_alpha)
+    sig = (np.arange(n_s + 1) - 0.5 * n_s) * ds
+    total = 0
+    for i in range(n_alpha):
+        if rows[i]:
+            x0 = cx + (sig + cy * sa[i]) / ca[i]
+            d, n_steps, limit = -sa[i] / ca[i], H, W
+        else:
+            x0 = cy + (sig + cx * ca[i]) / sa[i]
+            d, n_steps, limit = -ca[i] / sa[i], W, H
+        if abs(d) < 1e-12:
+            cnt = np.where((x0 > -1) & (x0 < limit), n_steps, 0)
+        else:
+            t1, t2 = (-1 - x0) / d, (limit - x0) / d
+            lo, hi = np.minimum(t1, t2), np.maximum(t1, t2)
+            first = np.maximum(np.floor(lo) + 1, 0)
+            last = np.minimum(np.ceil(hi) - 1, n_steps - 1)
+            cnt = np.maximum(last - first + 1, 0)
+        total += int(cnt.sum())
+    return total * cfg.n_views
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.proc = None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", self.gpu_id],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def max_over_ranks(pg, x: float, device) -> float:
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU baseline
+def oracle_sample(cfg, scan, n_views_sample: int, n_threads: int):
+    """Times the oracle on a bounded sample of the workload: the dRadon/ds of
+    n_views_sample views and the ECC of all pairs among them; extrapolates the
+    per-view and per-pair costs to the whole job."""
+    from oracle import oracle as orc
+    idx = np.linspace(0, cfg.n_views - 1, n_views_sample).round().astype(int)
+    P = scan["P"][idx]
+    imgs = scan["images"][idx]
+    t0 = time.perf_counter()
+    S = orc.radon_derivative(P, imgs, cfg.n_alpha, cfg.n_s, n_threads=n_threads)
+    t1 = time.perf_counter()
+    r = orc.ecc(P, S, cfg.W, cfg.H, cfg.K, n_threads=n_threads)
+    t2 = time.perf_counter()
+    n_pairs_sample = len(r["d"])
+    t_job = (t1 - t0) / n_views_sample * cfg.n_views + (t2 - t1) / n_pairs_sample * cfg.n_pairs
+    value = cfg.n_pairs * cfg.K / t_job
+    return value, {"radon_s": t1 - t0, "ecc_s": t2 - t1, "views": n_views_sample, "pairs": n_pairs_sample,
+                   "job_s_extrapolated": t_job}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cfg = synth.CONFIGS[args.workload]
+    scan = synth.make_scan(cfg)
+    cores = os.cpu_count() or 1
+    vals, infos = [], []
+    for it in range(args.warmup + args.steps):
+        v, info = oracle_sample(cfg, scan, 12, cores)
+        if it >= args.warmup:
+            vals.append(v)
+            infos.append(info)
+    value = statistics.median(vals)
+    ms = cfg.n_pairs * cfg.K / value * 1e3
+    sample = (f"per step: dRadon/ds of 12 of the {cfg.n_views} views and the ECC of the 66 pairs among them, "
+              f"extrapolated per view and per pair to the whole job")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(cfg),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    import paper_1806_02637_gb300 as ecc
+
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = synth.CONFIGS[args.workload]
+    scan = synth.make_scan(cfg)
+    ctx = ecc.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    P = torch.from_numpy(scan["P"]).to(dev)
+    images = torch.from_numpy(scan["images"]).to(dev)
+    sino = torch.empty((cfg.n_views, cfg.n_alpha, cfg.n_s), dtype=torch.float32, device=dev)
+    total = torch.empty((1,), dtype=torch.float64, device=dev)
+
+    def step():
+        ecc.ecc_precompute_radon_derivative(ctx, P, images, cfg.n_alpha, cfg.n_s, out=sino)
+        ecc.ecc_evaluate(ctx, P, sino, cfg.W, cfg.H, cfg.K, total=total, want_per_pair=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    ecc.ecc_profile_read(ctx)               # drop anything recorded so far
+    ecc.ecc_profile_enable(ctx, True)
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = str(local)
+    sampler = ClockSampler(gpu_id) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    launches0 = ecc.ecc_kernel_launches(ctx)
+    if pg is not None:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if pg is not None:
+        pg.barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    launches = ecc.ecc_kernel_launches(ctx) - launches0
+    prof = ecc.ecc_profile_read(ctx)
+    ecc.ecc_profile_enable(ctx, False)
+    clocks = sampler.stop() if sampler else None
+    result_total = float(total.cpu()[0])
+    elapsed_ms = max_over_ranks(pg, elapsed_ms, dev)
+    ms_per_step = elapsed_ms / args.steps
+    units = cfg.n_pairs * cfg.K
+    value = units * world / (ms_per_step / 1e3)
+
+    # ---------------- end to end through the host-buffer entry point
+    P_host = torch.from_numpy(scan["P"]).pin_memory()
+    img_host = torch.from_numpy(scan["images"]).pin_memory()
+    for _ in range(2):
+        ecc.ecc_scan_consistency_host(ctx, P_host, img_host, cfg.n_alpha, cfg.n_s, cfg.K)
+    if pg is not None:
+        pg.barrier()
+    e_steps = max(3, min(args.steps, 10))
+    t0 = time.perf_counter()
+    e_total = None
+    for _ in range(e_steps):
+        e_total = ecc.ecc_scan_consistency_host(ctx, P_host, img_host, cfg.n_alpha, cfg.n_s, cfg.K)
+    e_s = time.perf_counter() - t0
+    e_s = max_over_ranks(pg, e_s, dev)
+    e2e = {"value": units * world / (e_s / e_steps), "unit": UNIT, "steps": e_steps,
+           "ms_per_step": e_s / e_steps * 1e3,
+           "h2d_bytes_per_step": int(scan["images"].nbytes + scan["P"].nbytes), "d2h_bytes_per_step": 8,
+           "api": "ecc_scan_consistency_host (pinned host buffers, synchronous)",
+           "total_matches_device_path": bool(e_total == result_total)}
+
+    if rank != 0:
+        return 0
+
+    # ---------------- per-kernel shares and the dominant kernel's roofline
+    kern = {}
+    tot_prof = sum(ms for _, ms in prof.values()) or 1.0
+    for name, (n, ms) in sorted(prof.items(), key=lambda kv: -kv[1][1]):
+        kern[name] = {"launches_per_step": n / args.steps, "ms_per_step": ms / args.steps, "share": ms / tot_prof}
+    dom = max(prof.items(), key=lambda kv: kv[1][1])[0]
+    peaks = measured_peaks()
+    n_dom, ms_dom = prof[dom]
+    if dom == "joseph_kernel":
+        taps = joseph_taps(cfg)
+        flops = FLOPS_PER_TAP * taps * args.steps / n_dom
+        achieved = flops / (ms_dom / n_dom / 1e3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP32 lanes x FMA x max SM clock (152 x 128 x 2 x 2.07 GHz)",
+                "work": f"{FLOPS_PER_TAP} FLOP per in-image Joseph tap, {taps} taps per step"}
+    else:
+        bytes_per_launch = 32.0 * units * args.steps / n_dom
+        achieved = bytes_per_launch / (ms_dom / n_dom / 1e3) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
+                "work": "32 B (2 views x 4 taps x FP32) per line-pair sample"}
+    ev_names = ("view_setup_kernel", "alpha_dir_kernel", "pair_setup_kernel", "ecc_pair_kernel", "reduce_kernel")
+    eval_ms = sum(kern[n]["ms_per_step"] for n in ("alpha_dir_kernel", "pair_setup_kernel", "ecc_pair_kernel",
+                                                   "reduce_kernel") if n in kern)
+    pk = kern.get("ecc_pair_kernel")
+    eval_only = None
+    if pk:
+        gbs = 32.0 * units / (pk["ms_per_step"] / 1e3) / 1e9
+        eval_only = {"ms_per_step": eval_ms, "line_pairs_per_s": units / (eval_ms / 1e3),
+                     "pair_kernel_ms": pk["ms_per_step"],
+                     "pair_kernel_gather_gbs": gbs,
+                     "pair_kernel_frac_of_hbm": gbs / peaks.get("hbm_gbs", 6800.0)}
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cores = os.cpu_count() or 1
+        v, info = oracle_sample(cfg, scan, 48, cores)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": (f"dRadon/ds of {info['views']} of the {cfg.n_views} views ({info['radon_s']:.1f} s) and ECC "
+                          f"of the {info['pairs']} pairs among them ({info['ecc_s']:.1f} s), extrapolated per view "
+                          f"and per pair to the whole job ({info['job_s_extrapolated']:.0f} s)")}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(cfg),
+            "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+            "kernels": kern, "ecc_eval_only": eval_only, "total": result_total,
+            "geometry_precision": "f64 set-up and anchors, f32 per-sample"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

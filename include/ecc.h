@@ -1,0 +1,174 @@
+/*
+ * ecc.h -- C ABI of the GB300 epipolar-consistency library (libecc.so).
+ *
+ * Computes the epipolar consistency metric of a cone-beam scan as defined in
+ * Preuhs, Manhart, Maier, "Fast Epipolar Consistency without the Need for Pseudo
+ * Matrix Inverses" (arXiv 1806.02637): the Grangeat intermediate function S of
+ * every projection (Eq. 1), and for every pair of projections the mean squared
+ * difference of S along the epipolar line pairs of the planes through both
+ * sources (Eq. 15), with the Cauchy norm (Eq. 16), summed over pairs (Eq. 17).
+ * Epipolar lines are built without any matrix inverse (Eq. 13/14).
+ *
+ * Conventions (all entry points)
+ *   - Pointers marked "device" must be CUDA device memory of the context's device;
+ *     "host" pointers are ordinary host memory.  The caller owns every buffer it
+ *     passes; the library never frees caller memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Every call except ecc_create/ecc_destroy/ecc_last_error/
+ *     ecc_status is asynchronous on that stream: outputs are valid once the
+ *     stream has reached the end of the call.
+ *   - Return value: ECC_OK (0) or a negative error code; on error a message is
+ *     available from ecc_last_error(), no output has been written, and the
+ *     context stays usable.  Errors that only the device can see (a degenerate
+ *     projection matrix, coincident sources) do not fail the call: the affected
+ *     pairs report N_kappa = 0, d = e = 0, and a status bit is set that
+ *     ecc_status() returns.
+ *   - A context serves one host thread at a time; calls on one context must be
+ *     issued on one stream (its scratch memory is reused across calls).
+ *
+ * Geometry
+ *   P[n_views][12]: FP64, row-major 3x4 projection matrices mapping homogeneous
+ *   world points [mm] to homogeneous detector pixels; pixel (i = column, j = row)
+ *   has its centre at (i, j).  Any non-zero scale and sign of each P is accepted.
+ *   Detectors are W columns x H rows, square pixels, no skew.
+ *
+ * Sinogram layout
+ *   sino[n_views][n_alpha][n_s] of the element type `dtype`; row m holds
+ *   alpha_m = m pi / n_alpha, column n holds s_n = (n - (n_s-1)/2) ds with
+ *   ds = sqrt(W^2 + H^2) / (n_s - 1) pixels, s measured from the detector centre
+ *   ((W-1)/2, (H-1)/2) along (cos alpha, sin alpha).
+ */
+#ifndef ECC_H_
+#define ECC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ecc_ctx ecc_ctx;
+
+enum {
+  ECC_OK = 0,
+  ECC_EINVAL = -1,   /* invalid argument */
+  ECC_ENOMEM = -2,   /* device allocation failed */
+  ECC_ECUDA = -3,    /* CUDA runtime error */
+  ECC_ETIMEOUT = -4, /* a bounded device wait gave up */
+  ECC_EADMIT = -5,   /* request does not fit the memory budget */
+  ECC_EPENDING = 1   /* result not ready yet */
+};
+
+enum { ECC_F32 = 0, ECC_F16 = 1, ECC_BF16 = 2 };
+
+/* Device status bits returned by ecc_status(). */
+enum { ECC_STATUS_DEGENERATE_VIEW = 1, ECC_STATUS_DEGENERATE_PAIR = 2 };
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int ecc_version(void);
+
+/* Creates a context on CUDA device `device`.  hbm_budget_bytes bounds the
+ * scratch memory the context may hold (0 = no bound).  *out receives the
+ * context.  Returns ECC_EINVAL for a bad device, ECC_ECUDA otherwise. */
+int ecc_create(ecc_ctx** out, int device, size_t hbm_budget_bytes);
+
+/* Frees the context and its scratch memory (waits for its work to finish). */
+void ecc_destroy(ecc_ctx* ctx);
+
+/* Message of the last error on this context (or of the last ecc_create failure
+ * when ctx is NULL).  Valid until the next call on the same context. */
+const char* ecc_last_error(const ecc_ctx* ctx);
+
+/* Waits for `stream`, then returns the device status bits accumulated by the
+ * calls issued so far (ECC_STATUS_*) in *flags and clears them. */
+int ecc_status(ecc_ctx* ctx, void* stream, int* flags);
+
+/* Number of kernels this context has launched since it was created. */
+long long ecc_kernel_launches(const ecc_ctx* ctx);
+
+/* Per-kernel timing.  While enabled, every kernel launch of the context is
+ * bracketed by two CUDA events recorded on its launch stream (adds two event
+ * records per launch).  ecc_profile_read waits for `stream`, then writes up to
+ * max_entries rows: names (32 bytes each, NUL-terminated, host memory), number
+ * of launches and summed milliseconds per kernel name; *n_entries receives the
+ * row count.  Reading clears the record. */
+int ecc_profile_enable(ecc_ctx* ctx, int enable);
+int ecc_profile_read(ecc_ctx* ctx, void* stream, int max_entries, char* names, long long* launches,
+                     double* total_ms, int* n_entries);
+
+/*
+ * S_lambda for every view: the Grangeat intermediate function (Eq. 1), i.e. the
+ * derivative with respect to the plane offset of the 3-D Radon transform on the
+ * planes through the source, computed from the projection: the projection is
+ * pre-weighted by D / sqrt(D^2 + u^2 + v^2) (u, v from the principal point, D
+ * the source-detector distance, all in pixels, taken from P), integrated along
+ * the detector lines of the (alpha, s) grid by Joseph's method (unit steps over
+ * rows when |cos alpha| >= |sin alpha|, else over columns, linear interpolation,
+ * zero outside the detector), differenced over a half step on either side of
+ * s_n, and weighted by (D^2 + s_pp^2) / D^2 (s_pp: distance of the line from the
+ * principal point).
+ *
+ *   P        device, FP64 [n_views][12]
+ *   images   device, FP32 [n_views][H][W] line-integral projections
+ *   sino_out device, [n_views][n_alpha][n_s] of dtype (ECC_F32, ECC_F16, ECC_BF16)
+ *   scales_out device FP32 [n_views] or NULL: per-view scale factors of F16
+ *            storage (stored value = S / scale); NULL for F32/BF16
+ * Limits: 2 <= W, H <= 16384; 4 <= n_alpha <= 65535; 2 <= n_s <= 65535.
+ */
+int ecc_precompute_radon_derivative(ecc_ctx* ctx, int n_views, const double* P, const float* images, int W, int H,
+                                    int n_alpha, int n_s, int dtype, void* sino_out, float* scales_out,
+                                    void* stream);
+
+/*
+ * Epipolar consistency over a list of view pairs (Eq. 15-17).
+ *
+ * For each pair (a, b) the pencil of epipolar planes around the baseline C_a C_b
+ * is parametrised by an angle kappa in a frame built from the baseline and the
+ * two detectors' up axes; each plane's line in view lambda is l = cof(M) n
+ * (Eq. 13/14; no inverse).  The arc of kappa whose lines meet view a's detector
+ * and the arc for view b are found from the detector corners; the shorter arc is
+ * sampled at n_kappa midpoints kappa_k = lo + (k + 1/2) len / n_kappa and a
+ * sample counts if its plane meets both detectors (N_kappa of Eq. 15).  S_a and
+ * S_b are bilinear look-ups in the (alpha, s) grid (alpha folded into [0, pi)
+ * with S(alpha + pi, s) = -S(alpha, -s)).
+ *   d_ab = (1/N_kappa) sum_k (S_a - S_b)^2   (0 if N_kappa = 0)
+ *   e_ab = d_ab / (1 + d_ab / c)            (c = cauchy_c; c <= 0 gives e = d)
+ *   total = sum over the pairs of e_ab       (FP64, fixed summation order)
+ *
+ *   P        device FP64 [n_views][12]
+ *   motion   device FP64 [n_views][6] or NULL: per-view rigid motion theta =
+ *            (rx, ry, rz [rad], tx, ty, tz [mm]); the view uses P T(theta) with
+ *            T = [R t; 0 1], R = Rz(rz) Ry(ry) Rx(rx) (motion model of the
+ *            Optimization section).  NULL = no motion.
+ *   sino     device [n_views][n_alpha][n_s] of dtype; scales device FP32
+ *            [n_views] for ECC_F16 (as written by the precompute), else NULL
+ *   pairs    device int32 [n_pairs][2] or NULL = all a < b in row-major order
+ *            (then n_pairs must equal n_views (n_views - 1) / 2)
+ *   total    device FP64 [1]
+ *   per_pair device FP64 [n_pairs][2] = {d, e} or NULL
+ *   nkappa   device int32 [n_pairs] or NULL
+ * Arithmetic: geometry (per view, per pair, per 32-sample anchor) in FP64;
+ * per-sample line offsets, interpolation and accumulation in FP32.
+ * Limits: 1 <= n_kappa <= 65536; 0 <= n_pairs <= 2^31 - 1.
+ */
+int ecc_evaluate(ecc_ctx* ctx, int n_views, const double* P, const double* motion, const void* sino,
+                 const float* scales, int W, int H, int n_alpha, int n_s, int dtype, int n_kappa, double cauchy_c,
+                 const int32_t* pairs, int n_pairs, double* total, double* per_pair, int32_t* nkappa, void* stream);
+
+/*
+ * End-to-end evaluation from host buffers: copies P (host FP64 [n_views][12]) and
+ * the projections (host FP32 [n_views][H][W], pinned memory recommended) to the
+ * device, computes the sinograms (ECC_F32, kept in the context) and the total
+ * over all pairs a < b, and copies the total back into *total_host.  Synchronous:
+ * returns after the result is on the host.
+ */
+int ecc_scan_consistency_host(ecc_ctx* ctx, int n_views, const double* P_host, const float* images_host, int W,
+                              int H, int n_alpha, int n_s, int n_kappa, double cauchy_c, double* total_host,
+                              void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ECC_H_ */

@@ -1,0 +1,275 @@
+"""GB300 epipolar-consistency (ECC) library: Python binding of libecc.so.
+
+Thin argument marshalling over the C ABI declared in include/ecc.h; every step of
+the computation runs in the library's CUDA kernels.  PyTorch is used only for
+device memory and streams.  There is no CPU fallback: if the library is missing
+or no GPU is present the calls raise.
+
+Entry points (same names as the C ABI):
+    ecc_precompute_radon_derivative  S_lambda of every projection (Eq. 1)
+    ecc_evaluate                     d, e per pair and the total (Eq. 15-17)
+    ecc_scan_consistency_host        end to end from host buffers
+    ecc_status                       device-side status bits
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["EccError", "Context", "library_path", "load", "ecc_precompute_radon_derivative", "ecc_evaluate",
+           "ecc_scan_consistency_host", "ecc_status", "ecc_kernel_launches", "ecc_profile_enable",
+           "ecc_profile_read", "ECC_F32", "ECC_F16", "ECC_BF16"]
+
+ECC_F32, ECC_F16, ECC_BF16 = 0, 1, 2
+ECC_OK = 0
+
+_lock = threading.Lock()
+_lib = None
+
+
+class EccError(RuntimeError):
+    pass
+
+
+def library_path() -> str:
+    return _build.SO
+
+
+def load(build_if_missing: bool = True):
+    """Loads libecc.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(_build.SO):
+            raise EccError(f"libecc.so is not built ({_build.SO})")
+        lib = ctypes.CDLL(_build.SO)
+        vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+        lib.ecc_version.restype = i
+        lib.ecc_create.argtypes = [ctypes.POINTER(vp), i, sz]
+        lib.ecc_create.restype = i
+        lib.ecc_destroy.argtypes = [vp]
+        lib.ecc_destroy.restype = None
+        lib.ecc_last_error.argtypes = [vp]
+        lib.ecc_last_error.restype = ctypes.c_char_p
+        lib.ecc_status.argtypes = [vp, vp, ctypes.POINTER(i)]
+        lib.ecc_status.restype = i
+        lib.ecc_precompute_radon_derivative.argtypes = [vp, i, vp, vp, i, i, i, i, i, vp, vp, vp]
+        lib.ecc_precompute_radon_derivative.restype = i
+        lib.ecc_evaluate.argtypes = [vp, i, vp, vp, vp, vp, i, i, i, i, i, i, d, vp, i, vp, vp, vp, vp]
+        lib.ecc_evaluate.restype = i
+        lib.ecc_scan_consistency_host.argtypes = [vp, i, vp, vp, i, i, i, i, i, d, ctypes.POINTER(d), vp]
+        lib.ecc_scan_consistency_host.restype = i
+        lib.ecc_kernel_launches.argtypes = [vp]
+        lib.ecc_kernel_launches.restype = ctypes.c_longlong
+        lib.ecc_profile_enable.argtypes = [vp, i]
+        lib.ecc_profile_enable.restype = i
+        lib.ecc_profile_read.argtypes = [vp, vp, i, ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong),
+                                         ctypes.POINTER(d), ctypes.POINTER(i)]
+        lib.ecc_profile_read.restype = i
+        _lib = lib
+        return lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype_code(dt) -> int:
+    torch = _torch()
+    table = {torch.float32: ECC_F32, torch.float16: ECC_F16, torch.bfloat16: ECC_BF16}
+    if dt not in table:
+        raise EccError(f"unsupported sinogram dtype {dt}")
+    return table[dt]
+
+
+def _check(ctx, rc, what):
+    if rc != ECC_OK:
+        msg = load().ecc_last_error(ctx.handle if ctx is not None else None)
+        raise EccError(f"{what} failed ({rc}): {msg.decode() if msg else ''}")
+
+
+def _dev(t, dtype, name, shape=None):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise EccError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise EccError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise EccError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise EccError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """Owns a library context (device scratch memory) on one CUDA device."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        lib = load()
+        h = ctypes.c_void_p()
+        rc = lib.ecc_create(ctypes.byref(h), int(device), int(hbm_budget_bytes))
+        if rc != ECC_OK:
+            msg = lib.ecc_last_error(None)
+            raise EccError(f"ecc_create failed ({rc}): {msg.decode() if msg else ''}")
+        self.handle = h
+        self.device = int(device)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().ecc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def ecc_precompute_radon_derivative(ctx: Context, P, images, n_alpha: int, n_s: int, dtype=None, out=None,
+                                    scales=None, stream=None):
+    """S_lambda on the (alpha, s) grid for every view.  P: CUDA float64 [N,3,4];
+    images: CUDA float32 [N,H,W].  Returns (sino [N,n_alpha,n_s], scales or None)."""
+    torch = _torch()
+    dtype = dtype or torch.float32
+    code = _dtype_code(dtype)
+    images = _dev(images, torch.float32, "images")
+    N, H, W = images.shape
+    P = _dev(P, torch.float64, "P", (N, 3, 4))
+    if out is None:
+        out = torch.empty((N, n_alpha, n_s), dtype=dtype, device=images.device)
+    _dev(out, dtype, "out", (N, n_alpha, n_s))
+    if code == ECC_F16:
+        if scales is None:
+            scales = torch.empty((N,), dtype=torch.float32, device=images.device)
+        _dev(scales, torch.float32, "scales", (N,))
+    else:
+        scales = None
+    rc = load().ecc_precompute_radon_derivative(ctx.handle, N, _ptr(P), _ptr(images), W, H, int(n_alpha), int(n_s),
+                                                code, _ptr(out), _ptr(scales), _stream(stream))
+    _check(ctx, rc, "ecc_precompute_radon_derivative")
+    return out, scales
+
+
+def ecc_evaluate(ctx: Context, P, sino, W: int, H: int, n_kappa: int, cauchy_c: float = 0.0, motion=None,
+                 pairs=None, scales=None, total=None, per_pair=None, nkappa=None, want_per_pair: bool = True,
+                 stream=None) -> dict:
+    """Consistency over pairs (all a < b if pairs is None).  Returns CUDA tensors
+    total [1] float64, per_pair [n_pairs, 2] float64 (d, e) and nkappa [n_pairs] int32."""
+    torch = _torch()
+    code = _dtype_code(sino.dtype)
+    N = sino.shape[0]
+    sino = _dev(sino, sino.dtype, "sino")
+    n_alpha, n_s = sino.shape[1], sino.shape[2]
+    P = _dev(P, torch.float64, "P", (N, 3, 4))
+    dev = sino.device
+    if motion is not None:
+        motion = _dev(motion, torch.float64, "motion", (N, 6))
+    if pairs is not None:
+        pairs = _dev(pairs, torch.int32, "pairs")
+        if pairs.dim() != 2 or pairs.shape[1] != 2:
+            raise EccError("pairs must be [n_pairs, 2]")
+        n_pairs = pairs.shape[0]
+    else:
+        n_pairs = N * (N - 1) // 2
+    if code == ECC_F16:
+        scales = _dev(scales, torch.float32, "scales", (N,))
+    else:
+        scales = None
+    if total is None:
+        total = torch.empty((1,), dtype=torch.float64, device=dev)
+    _dev(total, torch.float64, "total", (1,))
+    if want_per_pair:
+        if per_pair is None:
+            per_pair = torch.empty((n_pairs, 2), dtype=torch.float64, device=dev)
+        if nkappa is None:
+            nkappa = torch.empty((n_pairs,), dtype=torch.int32, device=dev)
+        _dev(per_pair, torch.float64, "per_pair", (n_pairs, 2))
+        _dev(nkappa, torch.int32, "nkappa", (n_pairs,))
+    rc = load().ecc_evaluate(ctx.handle, N, _ptr(P), _ptr(motion), _ptr(sino), _ptr(scales), int(W), int(H), n_alpha,
+                             n_s, code, int(n_kappa), float(cauchy_c), _ptr(pairs), int(n_pairs), _ptr(total),
+                             _ptr(per_pair), _ptr(nkappa), _stream(stream))
+    _check(ctx, rc, "ecc_evaluate")
+    return {"total": total, "per_pair": per_pair, "nkappa": nkappa}
+
+
+def ecc_scan_consistency_host(ctx: Context, P, images, n_alpha: int, n_s: int, n_kappa: int,
+                              cauchy_c: float = 0.0, stream=None) -> float:
+    """End to end from host arrays (numpy or CPU tensors; pinned tensors copy faster)."""
+    torch = _torch()
+    if isinstance(P, torch.Tensor):
+        P = P.detach().cpu().numpy()
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    if isinstance(images, torch.Tensor):
+        if images.is_cuda or images.dtype != torch.float32 or not images.is_contiguous():
+            raise EccError("images must be a contiguous CPU float32 tensor")
+        img_ptr, shape = images.data_ptr(), tuple(images.shape)
+    else:
+        images = np.ascontiguousarray(images, dtype=np.float32)
+        img_ptr, shape = images.ctypes.data, images.shape
+    N, H, W = shape
+    if P.shape != (N, 3, 4):
+        raise EccError("P must be [N, 3, 4]")
+    out = ctypes.c_double(0.0)
+    rc = load().ecc_scan_consistency_host(ctx.handle, N, ctypes.c_void_p(P.ctypes.data), ctypes.c_void_p(img_ptr),
+                                          W, H, int(n_alpha), int(n_s), int(n_kappa), float(cauchy_c),
+                                          ctypes.byref(out), _stream(stream))
+    _check(ctx, rc, "ecc_scan_consistency_host")
+    return out.value
+
+
+def ecc_status(ctx: Context, stream=None) -> int:
+    flags = ctypes.c_int(0)
+    rc = load().ecc_status(ctx.handle, _stream(stream), ctypes.byref(flags))
+    _check(ctx, rc, "ecc_status")
+    return flags.value
+
+
+def ecc_kernel_launches(ctx: Context) -> int:
+    """Number of kernels the context has launched so far."""
+    return int(load().ecc_kernel_launches(ctx.handle))
+
+
+def ecc_profile_enable(ctx: Context, enable: bool = True) -> None:
+    _check(ctx, load().ecc_profile_enable(ctx.handle, int(bool(enable))), "ecc_profile_enable")
+
+
+def ecc_profile_read(ctx: Context, stream=None, max_entries: int = 32) -> dict:
+    """{kernel name: (launches, summed ms)} since the last read (waits for the stream)."""
+    names = ctypes.create_string_buffer(32 * max_entries)
+    launches = (ctypes.c_longlong * max_entries)()
+    ms = (ctypes.c_double * max_entries)()
+    n = ctypes.c_int(0)
+    rc = load().ecc_profile_read(ctx.handle, _stream(stream), max_entries, names, launches, ms, ctypes.byref(n))
+    _check(ctx, rc, "ecc_profile_read")
+    out = {}
+    for k in range(n.value):
+        nm = names.raw[32 * k:32 * (k + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = (int(launches[k]), float(ms[k]))
+    return out

@@ -1,0 +1,413 @@
+// C ABI of the ECC library: context, argument validation, scratch memory and the
+// launch sequence of each entry point.  See include/ecc.h for the contract.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ecc.h"
+#include "ecc_internal.cuh"
+#include "kernels.cuh"
+
+namespace {
+
+struct Buf {
+  void* p = nullptr;
+  size_t n = 0;
+};
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct ProfRec {
+  const char* name;
+  cudaEvent_t b, e;
+};
+
+struct ecc_ctx {
+  long long launches = 0;
+  bool prof = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  int device = 0;
+  size_t budget = 0;
+  size_t held = 0;
+  std::string err;
+  int* d_status = nullptr;
+  Buf views, pairs, ctile, adir, perpair, nk, partial, rtable, wimg;
+  Buf h_P, h_img, h_sino, h_total;  // buffers of the host-buffer entry point
+};
+
+namespace {
+
+int fail(ecc_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  else g_create_error = buf;
+  return code;
+}
+
+int cuda_fail(ecc_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, ECC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Grow-only scratch allocation, bounded by the context budget.
+int ensure(ecc_ctx* c, Buf& b, size_t bytes, const char* name) {
+  if (bytes == 0) bytes = 16;
+  if (b.n >= bytes) return ECC_OK;
+  const size_t old = b.n;
+  if (c->budget && c->held - old + bytes > c->budget)
+    return fail(c, ECC_ENOMEM, "scratch '%s' of %zu bytes exceeds the context budget (%zu held of %zu)", name, bytes,
+                c->held, c->budget);
+  if (b.p) {
+    cudaFree(b.p);  // synchronises the device: no kernel still uses the old buffer
+    b.p = nullptr;
+    b.n = 0;
+    c->held -= old;
+  }
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    return fail(c, ECC_ENOMEM, "cudaMalloc of scratch '%s' (%zu bytes): %s", name, bytes, cudaGetErrorString(e));
+  }
+  b.n = bytes;
+  c->held += bytes;
+  return ECC_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+cudaEvent_t pooled_event(ecc_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+void hook_begin(void* vc, const char* name, cudaStream_t s) {
+  ecc_ctx* c = (ecc_ctx*)vc;
+  ++c->launches;
+  if (!c->prof) return;
+  cudaEvent_t b = pooled_event(c);
+  if (b) cudaEventRecord(b, s);
+  c->recs.push_back({name, b, nullptr});
+}
+
+void hook_end(void* vc, const char* name, cudaStream_t s) {
+  ecc_ctx* c = (ecc_ctx*)vc;
+  (void)name;
+  if (!c->prof || c->recs.empty()) return;
+  cudaEvent_t e = pooled_event(c);
+  if (e) cudaEventRecord(e, s);
+  c->recs.back().e = e;
+}
+
+ecc::LaunchHooks hooks_of(ecc_ctx* c) {
+  ecc::LaunchHooks h;
+  h.begin = hook_begin;
+  h.end = hook_end;
+  h.ctx = c;
+  return h;
+}
+
+int check_geometry_args(ecc_ctx* c, int n_views, const void* P, int W, int H, int n_alpha, int n_s, int dtype) {
+  if (n_views < 1) return fail(c, ECC_EINVAL, "n_views must be >= 1 (got %d)", n_views);
+  if (!P) return fail(c, ECC_EINVAL, "P is NULL");
+  if (W < 2 || H < 2 || W > 16384 || H > 16384) return fail(c, ECC_EINVAL, "detector %dx%d out of range", W, H);
+  if (n_alpha < 4 || n_alpha > 65535) return fail(c, ECC_EINVAL, "n_alpha %d out of range [4, 65535]", n_alpha);
+  if (n_s < 2 || n_s > 65535) return fail(c, ECC_EINVAL, "n_s %d out of range [2, 65535]", n_s);
+  if (dtype != ECC_F32 && dtype != ECC_F16 && dtype != ECC_BF16) return fail(c, ECC_EINVAL, "unknown dtype %d", dtype);
+  return ECC_OK;
+}
+
+__global__ void fill_kernel(float* p, int n, float v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+int run_precompute(ecc_ctx* c, int n_views, const double* P, const float* images, int W, int H, int n_alpha, int n_s,
+                   int dtype, void* sino_out, float* scales_out, cudaStream_t s) {
+  int rc;
+  if ((rc = ensure(c, c->views, sizeof(ecc::ViewRec) * (size_t)n_views, "views")) != ECC_OK) return rc;
+  const size_t tbytes = sizeof(ecc::RadonRow) * (size_t)n_views * n_alpha + sizeof(ecc::RadonView) * (size_t)n_views;
+  if ((rc = ensure(c, c->rtable, tbytes, "radon table")) != ECC_OK) return rc;
+  const size_t plane = (size_t)H * (W + 4) + (size_t)W * (H + 4);
+  const size_t max_batch_bytes = (size_t)256 << 20;
+  int batch = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_views, max_batch_bytes / (plane * 4)));
+  if ((rc = ensure(c, c->wimg, plane * 4 * (size_t)batch, "weighted images")) != ECC_OK) return rc;
+  const ecc::LaunchHooks hk = hooks_of(c);
+  hk.on_begin("view_setup_kernel", s);
+  ecc::view_setup_kernel<<<(n_views + 127) / 128, 128, 0, s>>>(n_views, P, nullptr, W, H, (ecc::ViewRec*)c->views.p,
+                                                              c->d_status);
+  hk.on_end("view_setup_kernel", s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "view set-up launch");
+  e = ecc::launch_radon((const ecc::ViewRec*)c->views.p, n_views, images, W, H, n_alpha, n_s, dtype, sino_out,
+                        scales_out, (ecc::RadonRow*)c->rtable.p, (float*)c->wimg.p, batch, hk, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "radon launch");
+  if (dtype == ECC_F16 && scales_out) {
+    hk.on_begin("fill_kernel", s);
+    fill_kernel<<<(n_views + 255) / 256, 256, 0, s>>>(scales_out, n_views, 1.0f);
+    hk.on_end("fill_kernel", s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "scale fill launch");
+  }
+  return ECC_OK;
+}
+
+int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion, const void* sino,
+                 const float* scales, int W, int H, int n_alpha, int n_s, int dtype, int n_kappa, double cauchy_c,
+                 const int32_t* pairs, int n_pairs, double* total, double* per_pair, int32_t* nkappa,
+                 cudaStream_t s) {
+  int rc;
+  cudaError_t e;
+  if (n_pairs == 0) {
+    e = cudaMemsetAsync(total, 0, sizeof(double), s);
+    return e == cudaSuccess ? ECC_OK : cuda_fail(c, e, "memset total");
+  }
+  const int n_tiles = (n_kappa + 31) / 32;
+  const long long np = n_pairs;
+  const long long n_blocks = (np + 7) / 8;
+  if ((rc = ensure(c, c->views, sizeof(ecc::ViewRec) * (size_t)n_views, "views")) != ECC_OK) return rc;
+  if ((rc = ensure(c, c->pairs, sizeof(ecc::PairRec) * (size_t)np, "pairs")) != ECC_OK) return rc;
+  if ((rc = ensure(c, c->ctile, sizeof(double2) * (size_t)np * n_tiles, "tile directions")) != ECC_OK) return rc;
+  if ((rc = ensure(c, c->adir, sizeof(double2) * (size_t)n_alpha, "alpha directions")) != ECC_OK) return rc;
+  if ((rc = ensure(c, c->partial, sizeof(double) * (size_t)n_blocks, "block partials")) != ECC_OK) return rc;
+  if (!per_pair) {
+    if ((rc = ensure(c, c->perpair, sizeof(double) * 2 * (size_t)np, "per-pair")) != ECC_OK) return rc;
+    per_pair = (double*)c->perpair.p;
+  }
+  const ecc::LaunchHooks hk = hooks_of(c);
+  hk.on_begin("view_setup_kernel", s);
+  ecc::view_setup_kernel<<<(n_views + 127) / 128, 128, 0, s>>>(n_views, P, motion, W, H, (ecc::ViewRec*)c->views.p,
+                                                              c->d_status);
+  hk.on_end("view_setup_kernel", s);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "view set-up launch");
+  hk.on_begin("alpha_dir_kernel", s);
+  ecc::alpha_dir_kernel<<<(n_alpha + 255) / 256, 256, 0, s>>>(n_alpha, (double2*)c->adir.p);
+  hk.on_end("alpha_dir_kernel", s);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "alpha table launch");
+  hk.on_begin("pair_setup_kernel", s);
+  ecc::pair_setup_kernel<<<(unsigned)((np + 127) / 128), 128, 0, s>>>(
+      n_views, np, pairs, (const ecc::ViewRec*)c->views.p, W, H, n_kappa, (ecc::PairRec*)c->pairs.p,
+      (double2*)c->ctile.p, n_tiles, c->d_status);
+  hk.on_end("pair_setup_kernel", s);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "pair set-up launch");
+  const double inv_ds = (double)(n_s - 1) / std::sqrt((double)W * W + (double)H * H);
+  int nb = 0;
+  e = ecc::launch_ecc_pairs(np, (const ecc::PairRec*)c->pairs.p, (const double2*)c->ctile.p, n_tiles,
+                            (const double2*)c->adir.p, sino, scales, dtype, n_alpha, n_s, n_kappa, inv_ds, cauchy_c,
+                            per_pair, nkappa, (double*)c->partial.p, &nb, hk, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "pair kernel launch");
+  e = ecc::launch_reduce((const double*)c->partial.p, nb, total, hk, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reduce launch");
+  return ECC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ecc_version(void) { return 100; }
+
+int ecc_create(ecc_ctx** out, int device, size_t hbm_budget_bytes) {
+  if (!out) return fail(nullptr, ECC_EINVAL, "out is NULL");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, ECC_ECUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
+  }
+  if (device < 0 || device >= n) return fail(nullptr, ECC_EINVAL, "device %d out of range (%d devices)", device, n);
+  DeviceGuard g(device);
+  ecc_ctx* c = new ecc_ctx();
+  c->device = device;
+  c->budget = hbm_budget_bytes;
+  e = cudaMalloc(&c->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return fail(nullptr, ECC_ECUDA, "context allocation: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return ECC_OK;
+}
+
+void ecc_destroy(ecc_ctx* c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  cudaDeviceSynchronize();
+  Buf* bufs[] = {&c->views, &c->pairs, &c->ctile, &c->adir, &c->perpair, &c->nk, &c->partial, &c->rtable, &c->wimg,
+                 &c->h_P, &c->h_img, &c->h_sino, &c->h_total};
+  for (Buf* b : bufs)
+    if (b->p) cudaFree(b->p);
+  if (c->d_status) cudaFree(c->d_status);
+  for (const ProfRec& r : c->recs) {
+    if (r.b) cudaEventDestroy(r.b);
+    if (r.e) cudaEventDestroy(r.e);
+  }
+  for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+  delete c;
+}
+
+const char* ecc_last_error(const ecc_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+int ecc_status(ecc_ctx* c, void* stream, int* flags) {
+  if (!c || !flags) return fail(c, ECC_EINVAL, "ctx or flags is NULL");
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "status read");
+  *flags = h;
+  return ECC_OK;
+}
+
+long long ecc_kernel_launches(const ecc_ctx* c) { return c ? c->launches : -1; }
+
+int ecc_profile_enable(ecc_ctx* c, int enable) {
+  if (!c) return fail(nullptr, ECC_EINVAL, "ctx is NULL");
+  c->prof = enable != 0;
+  return ECC_OK;
+}
+
+int ecc_profile_read(ecc_ctx* c, void* stream, int max_entries, char* names, long long* launches,
+                     double* total_ms, int* n_entries) {
+  if (!c || !n_entries || max_entries < 0 || (max_entries > 0 && (!names || !launches || !total_ms)))
+    return fail(c, ECC_EINVAL, "invalid profile_read arguments");
+  DeviceGuard g(c->device);
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "profile stream sync");
+  std::vector<std::string> nm;
+  std::vector<long long> cnt;
+  std::vector<double> ms;
+  for (const ProfRec& r : c->recs) {
+    float t = 0.0f;
+    if (r.b && r.e && cudaEventElapsedTime(&t, r.b, r.e) != cudaSuccess) {
+      cudaGetLastError();
+      t = 0.0f;
+    }
+    size_t k = 0;
+    while (k < nm.size() && nm[k] != r.name) ++k;
+    if (k == nm.size()) {
+      nm.push_back(r.name);
+      cnt.push_back(0);
+      ms.push_back(0.0);
+    }
+    cnt[k] += 1;
+    ms[k] += t;
+    if (r.b) c->pool.push_back(r.b);
+    if (r.e) c->pool.push_back(r.e);
+  }
+  c->recs.clear();
+  const int n = (int)std::min<size_t>(nm.size(), (size_t)max_entries);
+  for (int k = 0; k < n; ++k) {
+    std::snprintf(names + 32 * k, 32, "%s", nm[k].c_str());
+    launches[k] = cnt[k];
+    total_ms[k] = ms[k];
+  }
+  *n_entries = n;
+  return ECC_OK;
+}
+
+int ecc_precompute_radon_derivative(ecc_ctx* c, int n_views, const double* P, const float* images, int W, int H,
+                                    int n_alpha, int n_s, int dtype, void* sino_out, float* scales_out,
+                                    void* stream) {
+  if (!c) return fail(nullptr, ECC_EINVAL, "ctx is NULL");
+  int rc = check_geometry_args(c, n_views, P, W, H, n_alpha, n_s, dtype);
+  if (rc != ECC_OK) return rc;
+  if (!images || !sino_out) return fail(c, ECC_EINVAL, "images or sino_out is NULL");
+  if (dtype == ECC_F16 && !scales_out) return fail(c, ECC_EINVAL, "ECC_F16 needs scales_out");
+  DeviceGuard g(c->device);
+  return run_precompute(c, n_views, P, images, W, H, n_alpha, n_s, dtype, sino_out, scales_out,
+                        (cudaStream_t)stream);
+}
+
+int ecc_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion, const void* sino,
+                 const float* scales, int W, int H, int n_alpha, int n_s, int dtype, int n_kappa, double cauchy_c,
+                 const int32_t* pairs, int n_pairs, double* total, double* per_pair, int32_t* nkappa, void* stream) {
+  if (!c) return fail(nullptr, ECC_EINVAL, "ctx is NULL");
+  int rc = check_geometry_args(c, n_views, P, W, H, n_alpha, n_s, dtype);
+  if (rc != ECC_OK) return rc;
+  if (!sino || !total) return fail(c, ECC_EINVAL, "sino or total is NULL");
+  if (dtype == ECC_F16 && !scales) return fail(c, ECC_EINVAL, "ECC_F16 needs scales");
+  if (n_kappa < 1 || n_kappa > 65536) return fail(c, ECC_EINVAL, "n_kappa %d out of range [1, 65536]", n_kappa);
+  if (n_pairs < 0) return fail(c, ECC_EINVAL, "n_pairs %d < 0", n_pairs);
+  if (!pairs) {
+    const long long all = (long long)n_views * (n_views - 1) / 2;
+    if (all != n_pairs)
+      return fail(c, ECC_EINVAL, "pairs is NULL but n_pairs (%d) != n_views (n_views - 1) / 2 (%lld)", n_pairs, all);
+  }
+  if (!std::isfinite(cauchy_c)) return fail(c, ECC_EINVAL, "cauchy_c is not finite");
+  DeviceGuard g(c->device);
+  return run_evaluate(c, n_views, P, motion, sino, scales, W, H, n_alpha, n_s, dtype, n_kappa, cauchy_c, pairs,
+                      n_pairs, total, per_pair, nkappa, (cudaStream_t)stream);
+}
+
+int ecc_scan_consistency_host(ecc_ctx* c, int n_views, const double* P_host, const float* images_host, int W,
+                              int H, int n_alpha, int n_s, int n_kappa, double cauchy_c, double* total_host,
+                              void* stream) {
+  if (!c) return fail(nullptr, ECC_EINVAL, "ctx is NULL");
+  int rc = check_geometry_args(c, n_views, P_host, W, H, n_alpha, n_s, ECC_F32);
+  if (rc != ECC_OK) return rc;
+  if (!images_host || !total_host) return fail(c, ECC_EINVAL, "images_host or total_host is NULL");
+  if (n_views < 2) return fail(c, ECC_EINVAL, "need at least two views");
+  if (n_kappa < 1 || n_kappa > 65536) return fail(c, ECC_EINVAL, "n_kappa %d out of range [1, 65536]", n_kappa);
+  const long long np = (long long)n_views * (n_views - 1) / 2;
+  if (np > 0x7fffffffLL) return fail(c, ECC_EINVAL, "too many pairs");
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t pb = sizeof(double) * 12 * (size_t)n_views;
+  const size_t ib = sizeof(float) * (size_t)W * H * n_views;
+  const size_t sb = sizeof(float) * (size_t)n_alpha * n_s * n_views;
+  if ((rc = ensure(c, c->h_P, pb, "host-call P")) != ECC_OK) return rc;
+  if ((rc = ensure(c, c->h_img, ib, "host-call images")) != ECC_OK) return rc;
+  if ((rc = ensure(c, c->h_sino, sb, "host-call sinograms")) != ECC_OK) return rc;
+  if ((rc = ensure(c, c->h_total, sizeof(double), "host-call total")) != ECC_OK) return rc;
+  cudaError_t e = cudaMemcpyAsync(c->h_P.p, P_host, pb, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_img.p, images_host, ib, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
+  rc = run_precompute(c, n_views, (const double*)c->h_P.p, (const float*)c->h_img.p, W, H, n_alpha, n_s, ECC_F32,
+                      c->h_sino.p, nullptr, s);
+  if (rc != ECC_OK) return rc;
+  rc = run_evaluate(c, n_views, (const double*)c->h_P.p, nullptr, c->h_sino.p, nullptr, W, H, n_alpha, n_s, ECC_F32,
+                    n_kappa, cauchy_c, nullptr, (int)np, (double*)c->h_total.p, nullptr, nullptr, s);
+  if (rc != ECC_OK) return rc;
+  e = cudaMemcpyAsync(total_host, c->h_total.p, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
+  return ECC_OK;
+}
+
+}  // extern "C"

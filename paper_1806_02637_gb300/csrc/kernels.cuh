@@ -1,0 +1,58 @@
+// Kernel declarations shared by the translation units of the library.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "ecc_internal.cuh"
+
+namespace ecc {
+
+__global__ void view_setup_kernel(int n_views, const double* P, const double* motion, int W, int H, ViewRec* out,
+                                  int* status);
+__global__ void pair_setup_kernel(int n_views, long long n_pairs, const int32_t* pairs, const ViewRec* views, int W,
+                                  int H, int K, PairRec* out, double2* ctile, int n_tiles, int* status);
+__global__ void alpha_dir_kernel(int n_alpha, double2* dir);
+
+// Per (view, alpha-row) line parameters of the Joseph line sums (32.32 fixed point).
+struct RadonRow {
+  long long B0;    // coordinate along the interpolation axis at rho index 0, step 0
+  long long STEP;  // per rho index
+  long long DY;    // per step along the integration axis
+  float inv_len;   // path length per step: 1/|cos a| (rows) or 1/|sin a| (columns)
+  float ca, sa;    // cos, sin of alpha
+  int rows_mode;   // 1: step over image rows, interpolate in x; 0: columns
+};
+
+struct RadonView {  // per-view weights (FP32 copies of the FP64 set-up)
+  float u0, v0, D;
+  int pad;
+};
+
+// Callbacks around every kernel launch (launch counting and optional CUDA-event
+// timing by the context).
+struct LaunchHooks {
+  void (*begin)(void* ctx, const char* name, cudaStream_t s) = nullptr;
+  void (*end)(void* ctx, const char* name, cudaStream_t s) = nullptr;
+  void* ctx = nullptr;
+  void on_begin(const char* n, cudaStream_t s) const {
+    if (begin) begin(ctx, n, s);
+  }
+  void on_end(const char* n, cudaStream_t s) const {
+    if (end) end(ctx, n, s);
+  }
+};
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_radon(const ViewRec* views, int n_views, const float* images, int W, int H, int n_alpha, int n_s,
+                         int dtype, void* sino_out, float* scales_out, RadonRow* table, float* wimg,
+                         int batch_views, const LaunchHooks& hooks, cudaStream_t stream);
+
+cudaError_t launch_ecc_pairs(long long n_pairs, const PairRec* prs, const double2* ctile, int n_tiles,
+                             const double2* alpha_dir, const void* sino, const float* scales, int dtype,
+                             int n_alpha, int n_s, int K, double inv_ds, double cauchy_c, double* per_pair, int32_t* nk_out,
+                             double* block_partial, int* n_blocks_out, const LaunchHooks& hooks,
+                             cudaStream_t stream);
+
+cudaError_t launch_reduce(const double* partial, int n, double* total, const LaunchHooks& hooks,
+                          cudaStream_t stream);
+
+}  // namespace ecc

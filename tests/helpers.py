@@ -1,0 +1,59 @@
+"""Shared helpers of the parity tests: cached seeded workloads, oracle sinograms,
+per-pair energies and the tolerance measures (test infrastructure)."""
+from __future__ import annotations
+
+import functools
+
+import numpy as np
+
+import synth
+from oracle import oracle as orc
+
+# FP32 paths must match the FP64 oracle within this relative error (per pair the
+# denominator is max(d, FLOOR * E_ab), E_ab the mean of (S_a^2 + S_b^2)/2 over the
+# pair's valid planes: d is a difference of nearly equal values for consistent
+# pairs, and any FP32 arithmetic is only relative to E_ab there).
+TOL_F32 = 1e-5
+FLOOR = 1e-2
+
+
+@functools.lru_cache(maxsize=None)
+def scan(name: str, views: tuple | None = None):
+    cfg = synth.CONFIGS[name]
+    sc = synth.make_scan(cfg, views=None if views is None else np.array(views))
+    return sc
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_sino(name: str, views: tuple | None = None, n_alpha: int | None = None, n_s: int | None = None):
+    cfg = synth.CONFIGS[name]
+    sc = scan(name, views)
+    return orc.radon_derivative(sc["P"], sc["images"], n_alpha or cfg.n_alpha, n_s or cfg.n_s)
+
+
+def energies(P, sino, W, H, K, pairs, motion=None):
+    """E_ab for each pair, from the oracle with zero-sinogram copies of the views."""
+    P = np.asarray(P).reshape(-1, 3, 4)
+    n = P.shape[0]
+    P2 = np.concatenate([P, P])
+    S2 = np.concatenate([sino, np.zeros_like(sino)])
+    m2 = None if motion is None else np.concatenate([motion, motion])
+    pairs = np.asarray(pairs)
+    pa = np.stack([pairs[:, 0], pairs[:, 1] + n], axis=1)
+    pb = np.stack([pairs[:, 0] + n, pairs[:, 1]], axis=1)
+    ea = orc.ecc(P2, S2, W, H, K, motion=m2, pairs=pa)["d"]
+    eb = orc.ecc(P2, S2, W, H, K, motion=m2, pairs=pb)["d"]
+    return 0.5 * (ea + eb)
+
+
+def pair_rel_err(d_gpu, d_ref, E):
+    return np.abs(np.asarray(d_gpu) - np.asarray(d_ref)) / np.maximum(np.asarray(d_ref), FLOOR * np.asarray(E))
+
+
+def sino_rel_err(S_gpu, S_ref):
+    """Per view max|dS| / max|S|."""
+    S_gpu = np.asarray(S_gpu, dtype=np.float64)
+    S_ref = np.asarray(S_ref, dtype=np.float64)
+    num = np.abs(S_gpu - S_ref).reshape(S_ref.shape[0], -1).max(axis=1)
+    den = np.abs(S_ref).reshape(S_ref.shape[0], -1).max(axis=1)
+    return num / den

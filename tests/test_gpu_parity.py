@@ -1,0 +1,252 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same
+seeded inputs: sinograms (Eq. 1), per-pair d, e, N_kappa and totals (Eq. 15-17),
+edge cases, and full-size launches checked on sampled pairs."""
+import functools
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import oracle as orc
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@functools.lru_cache(maxsize=None)
+def _ctx():
+    import paper_1806_02637_gb300 as ecc
+    return ecc.Context(0)
+
+
+def _ecc():
+    import paper_1806_02637_gb300 as ecc
+    return ecc
+
+
+def _cuda(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def _gpu_sino(sc, n_alpha, n_s, dtype=None):
+    ecc = _ecc()
+    S, scales = ecc.ecc_precompute_radon_derivative(_ctx(), _cuda(sc["P"]), _cuda(sc["images"]), n_alpha, n_s,
+                                                    dtype=dtype)
+    torch.cuda.synchronize()
+    return S, scales
+
+
+def _gpu_eval(P, S_t, W, Hh, K, c=0.0, motion=None, pairs=None, scales=None):
+    ecc = _ecc()
+    r = ecc.ecc_evaluate(_ctx(), _cuda(P), S_t, W, Hh, K, cauchy_c=c,
+                         motion=None if motion is None else _cuda(motion),
+                         pairs=None if pairs is None else _cuda(np.asarray(pairs, dtype=np.int32)), scales=scales)
+    torch.cuda.synchronize()
+    return (float(r["total"].cpu()[0]), r["per_pair"].cpu().numpy(), r["nkappa"].cpu().numpy())
+
+
+# ----------------------------------------------------------------- sinograms
+@pytest.mark.parametrize("name,views", [("c1", None), ("c2", (0, 97, 250, 311, 495)), ("c3", (5, 200))])
+def test_radon_parity(name, views):
+    cfg = synth.CONFIGS[name]
+    sc = H.scan(name, views)
+    S, _ = _gpu_sino(sc, cfg.n_alpha, cfg.n_s)
+    ref = H.oracle_sino(name, views)
+    err = H.sino_rel_err(S.cpu().numpy(), ref)
+    assert err.max() <= H.TOL_F32, err
+
+
+def test_radon_parity_large_detector_ragged_grid():
+    """976^2 detector, 1024 x 1382 grid (n_s not a multiple of the 31-wide chunks)."""
+    cfg = synth.CONFIGS["c4"]
+    sc = H.scan("c4", (7,))
+    S, _ = _gpu_sino(sc, cfg.n_alpha, cfg.n_s)
+    ref = H.oracle_sino("c4", (7,))
+    assert H.sino_rel_err(S.cpu().numpy(), ref).max() <= H.TOL_F32
+
+
+@pytest.mark.parametrize("n_alpha,n_s", [(4, 2), (5, 3), (37, 61), (180, 129)])
+def test_radon_parity_small_grids(n_alpha, n_s):
+    sc = H.scan("c1")
+    S, _ = _gpu_sino(sc, n_alpha, n_s)
+    ref = orc.radon_derivative(sc["P"], sc["images"], n_alpha, n_s)
+    assert H.sino_rel_err(S.cpu().numpy(), ref).max() <= H.TOL_F32
+
+
+# --------------------------------------------------------------- ECC (Eq. 15-17)
+def _check_pairs(P, S32, W, Hh, K, c=0.0, motion=None, pairs=None):
+    """GPU vs oracle on the same FP32 sinogram values."""
+    total, pp, nk = _gpu_eval(P, _cuda(S32), W, Hh, K, c, motion, pairs)
+    ref = orc.ecc(P, S32.astype(np.float64), W, Hh, K, cauchy_c=c, motion=motion, pairs=pairs)
+    assert np.array_equal(nk, ref["nk"]), np.nonzero(nk != ref["nk"])
+    E = H.energies(P, S32.astype(np.float64), W, Hh, K, ref["pairs"], motion)
+    err_d = H.pair_rel_err(pp[:, 0], ref["d"], E)
+    err_e = H.pair_rel_err(pp[:, 1], ref["e"], E)
+    assert err_d.max() <= H.TOL_F32, (err_d.max(), np.argmax(err_d))
+    assert err_e.max() <= H.TOL_F32
+    assert abs(total - ref["total"]) <= H.TOL_F32 * abs(ref["total"]) + 1e-300
+    return total, pp, nk, ref
+
+
+def test_ecc_parity_c1_exact_and_moved():
+    cfg = synth.CONFIGS["c1"]
+    sc = H.scan("c1")
+    S32 = H.oracle_sino("c1").astype(np.float32)
+    _check_pairs(sc["P"], S32, cfg.W, cfg.H, cfg.K)
+    th = np.zeros((2, 6))
+    th[1] = [0.01, -0.004, 0.02, 0.5, -1.0, 1.5]
+    _check_pairs(sc["P"], S32, cfg.W, cfg.H, cfg.K, c=1e-3, motion=th)
+
+
+SUB = tuple(range(0, 496, 21))  # 24 views of the 496-view short scan
+
+
+@pytest.mark.parametrize("K", [512, 77, 1024, 1])
+def test_ecc_parity_short_scan_subset(K):
+    cfg = synth.CONFIGS["c2"]
+    sc = H.scan("c2", SUB)
+    S32 = H.oracle_sino("c2", SUB).astype(np.float32)
+    _check_pairs(sc["P"], S32, cfg.W, cfg.H, K)
+
+
+def test_ecc_parity_motion_cauchy_pair_list():
+    cfg = synth.CONFIGS["c3"]
+    views = tuple(range(0, 248, 11))
+    sc = H.scan("c3", views)
+    S32 = H.oracle_sino("c3", views).astype(np.float32)
+    rng = np.random.default_rng(3)
+    n = len(views)
+    pairs = np.array([(a, b) for a in range(n) for b in range(n) if a != b])[rng.choice(n * (n - 1), 150, False)]
+    _, pp, _, ref = _check_pairs(sc["P"], S32, cfg.W, cfg.H, cfg.K, c=0.0, motion=sc["motion"], pairs=pairs)
+    c = float(np.median(ref["d"]))
+    _check_pairs(sc["P"], S32, cfg.W, cfg.H, cfg.K, c=c, motion=sc["motion"], pairs=pairs)
+
+
+def test_ecc_full_scan_with_opposed_views():
+    """Full 360-degree geometry: opposed views take the full-pi arc branch."""
+    cfg = synth.CONFIGS["c4"]
+    views = (0, 1, 310, 619, 620, 621, 930, 1239)
+    sc = H.scan("c4", views)
+    S32 = orc.radon_derivative(sc["P"], sc["images"], 256, 346).astype(np.float32)
+    _, _, nk, ref = _check_pairs(sc["P"], S32, cfg.W, cfg.H, 256)
+    full = ref["arcs"][:, 2] > 3.14
+    assert full.any()
+
+
+def test_full_size_launch_sampled_pairs():
+    """All 122,760 pairs of the 496-view scan in one launch (the benchmark's
+    configuration); pairs among 40 sampled views are compared with the oracle on
+    oracle sinograms, the rest run on GPU-computed sinograms."""
+    cfg = synth.CONFIGS["c2"]
+    full = H.scan("c2")
+    views = tuple(int(v) for v in np.random.default_rng(496).choice(496, 40, replace=False))
+    S_all, _ = _gpu_sino(full, cfg.n_alpha, cfg.n_s)
+    S_or = H.oracle_sino("c2", tuple(sorted(views))).astype(np.float32)
+    idx = torch.tensor(sorted(views), device="cuda")
+    S_all[idx] = _cuda(S_or)
+    total, pp, nk = _gpu_eval(full["P"], S_all, cfg.W, cfg.H, cfg.K)
+    sv = np.array(sorted(views))
+    sub_pairs = np.array([(i, j) for i in range(40) for j in range(i + 1, 40)])
+    ga, gb = sv[sub_pairs[:, 0]], sv[sub_pairs[:, 1]]
+    n = 496
+    flat = ga * (2 * n - ga - 1) // 2 + (gb - ga - 1)
+    ref = orc.ecc(full["P"][sv], S_or.astype(np.float64), cfg.W, cfg.H, cfg.K, pairs=sub_pairs)
+    assert np.array_equal(nk[flat], ref["nk"])
+    E = H.energies(full["P"][sv], S_or.astype(np.float64), cfg.W, cfg.H, cfg.K, sub_pairs)
+    err = H.pair_rel_err(pp[flat, 0], ref["d"], E)
+    assert err.max() <= H.TOL_F32, err.max()
+    assert np.isfinite(pp).all() and (nk > 0).all() and (nk <= cfg.K).all()
+    assert np.isclose(total, pp[:, 1].sum(), rtol=1e-9)
+
+
+# ------------------------------------------------------------------ end to end
+def test_end_to_end_c1():
+    """Images -> sinograms -> total, both sides from the same images."""
+    cfg = synth.CONFIGS["c1"]
+    sc = H.scan("c1")
+    S, _ = _gpu_sino(sc, cfg.n_alpha, cfg.n_s)
+    th = np.zeros((2, 6))
+    th[1, 5] = 1.0
+    total, pp, nk = _gpu_eval(sc["P"], S, cfg.W, cfg.H, cfg.K, motion=th)
+    ref = orc.ecc(sc["P"], H.oracle_sino("c1"), cfg.W, cfg.H, cfg.K, motion=th)
+    assert np.array_equal(nk, ref["nk"])
+    assert abs(total - ref["total"]) <= H.TOL_F32 * ref["total"]
+
+
+def test_host_entry_matches_device_path():
+    ecc = _ecc()
+    cfg = synth.CONFIGS["c2"]
+    sc = H.scan("c2", SUB)
+    t_host = ecc.ecc_scan_consistency_host(_ctx(), sc["P"], sc["images"], cfg.n_alpha, cfg.n_s, cfg.K)
+    S, _ = _gpu_sino(sc, cfg.n_alpha, cfg.n_s)
+    t_dev, _, _ = _gpu_eval(sc["P"], S, cfg.W, cfg.H, cfg.K)
+    assert t_host == t_dev
+    ref = orc.ecc(sc["P"], H.oracle_sino("c2", SUB), cfg.W, cfg.H, cfg.K)["total"]
+    assert abs(t_host - ref) <= 1e-4 * ref
+
+
+def test_deterministic_and_pair_order():
+    cfg = synth.CONFIGS["c2"]
+    sc = H.scan("c2", SUB)
+    S32 = _cuda(H.oracle_sino("c2", SUB).astype(np.float32))
+    t1, p1, n1 = _gpu_eval(sc["P"], S32, cfg.W, cfg.H, cfg.K)
+    t2, p2, n2 = _gpu_eval(sc["P"], S32, cfg.W, cfg.H, cfg.K)
+    assert t1 == t2 and np.array_equal(p1, p2) and np.array_equal(n1, n2)
+    pairs = synth.upper_pairs(len(SUB))
+    t3, p3, n3 = _gpu_eval(sc["P"], S32, cfg.W, cfg.H, cfg.K, pairs=pairs)
+    assert np.array_equal(p1, p3) and np.array_equal(n1, n3)
+    # swapped pairs (b, a): same d up to the FP32 evaluation (the pencil is mirrored)
+    t4, p4, n4 = _gpu_eval(sc["P"], S32, cfg.W, cfg.H, cfg.K, pairs=pairs[:, ::-1].copy())
+    assert np.array_equal(n1, n4)
+    assert np.allclose(p1[:, 0], p4[:, 0], rtol=1e-4, atol=1e-6 * p1[:, 0].max())
+
+
+# ------------------------------------------------------------------ edge cases
+def test_degenerate_pair_and_status():
+    ecc = _ecc()
+    cfg = synth.CONFIGS["c1"]
+    sc = H.scan("c1")
+    P = np.stack([sc["P"][0], sc["P"][0] * 2.0, sc["P"][1]])   # views 0 and 1 share a source
+    S32 = np.concatenate([H.oracle_sino("c1")[:1], H.oracle_sino("c1")]).astype(np.float32)
+    ecc.ecc_status(_ctx())
+    total, pp, nk = _gpu_eval(P, _cuda(S32), cfg.W, cfg.H, cfg.K)
+    assert nk[0] == 0 and pp[0, 0] == 0.0
+    assert ecc.ecc_status(_ctx()) & 2
+    assert ecc.ecc_status(_ctx()) == 0
+    ref = orc.ecc(P[[0, 2]], S32[[0, 2]].astype(np.float64), cfg.W, cfg.H, cfg.K)
+    assert nk[1] == ref["nk"][0]
+
+
+def test_empty_pairs_and_invalid_arguments():
+    ecc = _ecc()
+    cfg = synth.CONFIGS["c1"]
+    sc = H.scan("c1")
+    S32 = _cuda(H.oracle_sino("c1").astype(np.float32))
+    r = ecc.ecc_evaluate(_ctx(), _cuda(sc["P"]), S32, cfg.W, cfg.H, cfg.K,
+                         pairs=torch.zeros((0, 2), dtype=torch.int32, device="cuda"))
+    torch.cuda.synchronize()
+    assert float(r["total"].cpu()[0]) == 0.0
+    with pytest.raises(ecc.EccError):
+        ecc.ecc_evaluate(_ctx(), _cuda(sc["P"]), S32, cfg.W, cfg.H, 0)
+    with pytest.raises(ecc.EccError):
+        ecc.ecc_evaluate(_ctx(), _cuda(sc["P"]), S32, 1, cfg.H, cfg.K)
+    # the context stays usable
+    total, _, _ = _gpu_eval(sc["P"], S32, cfg.W, cfg.H, cfg.K)
+    assert np.isfinite(total)
+
+
+def test_tiny_detector():
+    """5 x 7 detector, 8 x 9 grid: every tile and chunk is ragged."""
+    cfg = synth.ScanConfig("tiny", n_views=3, arc_deg=120.0, full_scan=False, W=7, H=5, pixel_mm=40.0,
+                           phantom="blobs", n_prim=1, size_range=(20.0, 25.0), value_range=(0.01, 0.02),
+                           n_alpha=8, n_s=9, K=40, seed=5)
+    sc = synth.make_scan(cfg)
+    S, _ = _gpu_sino(sc, cfg.n_alpha, cfg.n_s)
+    ref = orc.radon_derivative(sc["P"], sc["images"], cfg.n_alpha, cfg.n_s)
+    assert H.sino_rel_err(S.cpu().numpy(), ref).max() <= H.TOL_F32
+    _check_pairs(sc["P"], ref.astype(np.float32), cfg.W, cfg.H, cfg.K)
