@@ -168,13 +168,16 @@ static int arc_of_view(const view_t_r* vl, const view_t_r* vo, const double w[3]
 /* Arcs of a pair: {sampled view (0 = a, 1 = b), lo_s, len_s, lo_o, len_o}.  The
  * shorter of the two views' arcs is sampled (ties: view a) and masked by the
  * other (reading of the kappa range; the paper gives K samples with step
- * Delta kappa and counts the planes that hit both detectors). */
+ * Delta kappa and counts the planes that hit both detectors).  The two lengths
+ * are equal in exact arithmetic for mirror-symmetric pairs (a circular trajectory,
+ * also under shifts along its axis), so the tie is taken with a relative
+ * tolerance of 1e-9 instead of being left to rounding. */
 static int pair_arcs(const view_t_r* va, const view_t_r* vb, int W, int H, double arcs[5]) {
     double w[3], v[3], lo_a, len_a, lo_b, len_b;
     if (pair_frame_r(va, vb, w, v) != 0) return -1;
     if (arc_of_view(va, vb, w, v, va->C, W, H, &lo_a, &len_a) != 0) return -1;
     if (arc_of_view(vb, va, w, v, va->C, W, H, &lo_b, &len_b) != 0) return -1;
-    if (len_a <= len_b) {
+    if (len_a <= len_b + 1e-9 * fmax(len_a, len_b)) {
         arcs[0] = 0; arcs[1] = lo_a; arcs[2] = len_a; arcs[3] = lo_b; arcs[4] = len_b;
     } else {
         arcs[0] = 1; arcs[1] = lo_b; arcs[2] = len_b; arcs[3] = lo_a; arcs[4] = len_a;
