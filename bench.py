@@ -45,6 +45,9 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="c2", choices=["c2"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
+    ap.add_argument("--views", type=int, default=0,
+                    help="use the first N views of the workload (smaller case for profiling); 0 = all")
     return ap.parse_args()
 
 
@@ -230,7 +233,13 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     cfg = synth.CONFIGS[args.workload]
-    scan = synth.make_scan(cfg)
+    if args.views:
+        import dataclasses
+        full = cfg
+        cfg = dataclasses.replace(cfg, n_views=args.views)
+        scan = synth.make_scan(full, views=np.arange(args.views))
+    else:
+        scan = synth.make_scan(cfg)
     ctx = ecc.Context(local)
     stream = torch.cuda.current_stream(dev)
     P = torch.from_numpy(scan["P"]).to(dev)
@@ -277,25 +286,28 @@ def run_ours(args):
     units = cfg.n_pairs * cfg.K
     value = units * world / (ms_per_step / 1e3)
 
-    # ---------------- end to end through the host-buffer entry point
-    P_host = torch.from_numpy(scan["P"]).pin_memory()
-    img_host = torch.from_numpy(scan["images"]).pin_memory()
-    for _ in range(2):
-        ecc.ecc_scan_consistency_host(ctx, P_host, img_host, cfg.n_alpha, cfg.n_s, cfg.K)
-    if pg is not None:
-        pg.barrier()
-    e_steps = max(3, min(args.steps, 10))
-    t0 = time.perf_counter()
-    e_total = None
-    for _ in range(e_steps):
-        e_total = ecc.ecc_scan_consistency_host(ctx, P_host, img_host, cfg.n_alpha, cfg.n_s, cfg.K)
-    e_s = time.perf_counter() - t0
-    e_s = max_over_ranks(pg, e_s, dev)
-    e2e = {"value": units * world / (e_s / e_steps), "unit": UNIT, "steps": e_steps,
-           "ms_per_step": e_s / e_steps * 1e3,
-           "h2d_bytes_per_step": int(scan["images"].nbytes + scan["P"].nbytes), "d2h_bytes_per_step": 8,
-           "api": "ecc_scan_consistency_host (pinned host buffers, synchronous)",
-           "total_matches_device_path": bool(e_total == result_total)}
+    e2e = None
+    if not args.no_e2e:
+        # ---------------- end to end through the host-buffer entry point
+        P_host = torch.from_numpy(scan["P"]).pin_memory()
+        img_host = torch.from_numpy(scan["images"]).pin_memory()
+        for _ in range(2):
+            ecc.ecc_scan_consistency_host(ctx, P_host, img_host, cfg.n_alpha, cfg.n_s, cfg.K)
+        if pg is not None:
+            pg.barrier()
+        e_steps = max(3, min(args.steps, 10))
+        t0 = time.perf_counter()
+        e_total = None
+        for _ in range(e_steps):
+            e_total = ecc.ecc_scan_consistency_host(ctx, P_host, img_host, cfg.n_alpha, cfg.n_s, cfg.K)
+        e_s = time.perf_counter() - t0
+        e_s = max_over_ranks(pg, e_s, dev)
+        e2e = {"value": units * world / (e_s / e_steps), "unit": UNIT, "steps": e_steps,
+               "ms_per_step": e_s / e_steps * 1e3,
+               "h2d_bytes_per_step": int(scan["images"].nbytes + scan["P"].nbytes), "d2h_bytes_per_step": 8,
+               "api": "ecc_scan_consistency_host (pinned host buffers, synchronous)",
+               "total_matches_device_path": bool(e_total == result_total)}
+
 
     if rank != 0:
         return 0

@@ -112,8 +112,10 @@ int ecc_profile_read(ecc_ctx* ctx, void* stream, int max_entries, char* names, l
  *   P        device, FP64 [n_views][12]
  *   images   device, FP32 [n_views][H][W] line-integral projections
  *   sino_out device, [n_views][n_alpha][n_s] of dtype (ECC_F32, ECC_F16, ECC_BF16)
- *   scales_out device FP32 [n_views] or NULL: per-view scale factors of F16
- *            storage (stored value = S / scale); NULL for F32/BF16
+ *   scales_out device FP32 [n_views]: per-view scale factors of F16 storage,
+ *            scale = max|S| / 2^14 over the view (1 for an all-zero view), stored
+ *            value = S / scale rounded to FP16; required for ECC_F16, ignored
+ *            otherwise.  F32 and BF16 store S itself (BF16 rounded to nearest).
  * Limits: 2 <= W, H <= 16384; 4 <= n_alpha <= 65535; 2 <= n_s <= 65535.
  */
 int ecc_precompute_radon_derivative(ecc_ctx* ctx, int n_views, const double* P, const float* images, int W, int H,
@@ -155,6 +157,36 @@ int ecc_precompute_radon_derivative(ecc_ctx* ctx, int n_views, const double* P, 
 int ecc_evaluate(ecc_ctx* ctx, int n_views, const double* P, const double* motion, const void* sino,
                  const float* scales, int W, int H, int n_alpha, int n_s, int dtype, int n_kappa, double cauchy_c,
                  const int32_t* pairs, int n_pairs, double* total, double* per_pair, int32_t* nkappa, void* stream);
+
+/*
+ * As ecc_evaluate, plus the gradient of the total with respect to the per-view
+ * motion parameters theta (motion model of the Optimization section; theta = 0
+ * when motion is NULL), with the sampled planes (kappa arcs and validity) held at
+ * the evaluation point:
+ *   grad   device FP64 [n_views][6] = d total / d (rx, ry, rz, tx, ty, tz)
+ * Per-sample derivatives of the bilinear look-ups are cell-wise constant (FP32);
+ * the chain through the lines, the pencil frame, the sources and the cofactor
+ * matrices to theta is FP64 (forward-mode tangents).  The paper's optimiser is
+ * derivative-free; this gradient serves gradient-based motion estimation (the
+ * argmin of Eq. 17).
+ */
+int ecc_evaluate_grad(ecc_ctx* ctx, int n_views, const double* P, const double* motion, const void* sino,
+                      const float* scales, int W, int H, int n_alpha, int n_s, int dtype, int n_kappa,
+                      double cauchy_c, const int32_t* pairs, int n_pairs, double* total, double* per_pair,
+                      int32_t* nkappa, double* grad, void* stream);
+
+/*
+ * As ecc_evaluate, but the planes of every pair (kappa arcs, step and validity
+ * mask) are those sampled by the previous ecc_evaluate / ecc_evaluate_grad call on
+ * this context; only the geometry (P, motion) may change.  The arguments n_views,
+ * W, H, n_kappa, n_pairs and the pairs pointer must equal those of that call
+ * (ECC_EINVAL otherwise).  This is the function the gradient differentiates, used
+ * for finite-difference checks.
+ */
+int ecc_evaluate_frozen(ecc_ctx* ctx, int n_views, const double* P, const double* motion, const void* sino,
+                        const float* scales, int W, int H, int n_alpha, int n_s, int dtype, int n_kappa,
+                        double cauchy_c, const int32_t* pairs, int n_pairs, double* total, double* per_pair,
+                        int32_t* nkappa, void* stream);
 
 /*
  * End-to-end evaluation from host buffers: copies P (host FP64 [n_views][12]) and

@@ -22,6 +22,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["EccError", "Context", "library_path", "load", "ecc_precompute_radon_derivative", "ecc_evaluate",
+           "ecc_evaluate_grad", "ecc_evaluate_frozen", "consistency",
            "ecc_scan_consistency_host", "ecc_status", "ecc_kernel_launches", "ecc_profile_enable",
            "ecc_profile_read", "ECC_F32", "ECC_F16", "ECC_BF16"]
 
@@ -67,6 +68,10 @@ def load(build_if_missing: bool = True):
         lib.ecc_evaluate.restype = i
         lib.ecc_scan_consistency_host.argtypes = [vp, i, vp, vp, i, i, i, i, i, d, ctypes.POINTER(d), vp]
         lib.ecc_scan_consistency_host.restype = i
+        lib.ecc_evaluate_grad.argtypes = [vp, i, vp, vp, vp, vp, i, i, i, i, i, i, d, vp, i, vp, vp, vp, vp, vp]
+        lib.ecc_evaluate_grad.restype = i
+        lib.ecc_evaluate_frozen.argtypes = [vp, i, vp, vp, vp, vp, i, i, i, i, i, i, d, vp, i, vp, vp, vp, vp]
+        lib.ecc_evaluate_frozen.restype = i
         lib.ecc_kernel_launches.argtypes = [vp]
         lib.ecc_kernel_launches.restype = ctypes.c_longlong
         lib.ecc_profile_enable.argtypes = [vp, i]
@@ -177,16 +182,11 @@ def ecc_precompute_radon_derivative(ctx: Context, P, images, n_alpha: int, n_s: 
     return out, scales
 
 
-def ecc_evaluate(ctx: Context, P, sino, W: int, H: int, n_kappa: int, cauchy_c: float = 0.0, motion=None,
-                 pairs=None, scales=None, total=None, per_pair=None, nkappa=None, want_per_pair: bool = True,
-                 stream=None) -> dict:
-    """Consistency over pairs (all a < b if pairs is None).  Returns CUDA tensors
-    total [1] float64, per_pair [n_pairs, 2] float64 (d, e) and nkappa [n_pairs] int32."""
+def _eval_args(P, sino, motion, pairs, scales, total, per_pair, nkappa, want_per_pair):
     torch = _torch()
     code = _dtype_code(sino.dtype)
     N = sino.shape[0]
     sino = _dev(sino, sino.dtype, "sino")
-    n_alpha, n_s = sino.shape[1], sino.shape[2]
     P = _dev(P, torch.float64, "P", (N, 3, 4))
     dev = sino.device
     if motion is not None:
@@ -198,10 +198,7 @@ def ecc_evaluate(ctx: Context, P, sino, W: int, H: int, n_kappa: int, cauchy_c: 
         n_pairs = pairs.shape[0]
     else:
         n_pairs = N * (N - 1) // 2
-    if code == ECC_F16:
-        scales = _dev(scales, torch.float32, "scales", (N,))
-    else:
-        scales = None
+    scales = _dev(scales, torch.float32, "scales", (N,)) if code == ECC_F16 else None
     if total is None:
         total = torch.empty((1,), dtype=torch.float64, device=dev)
     _dev(total, torch.float64, "total", (1,))
@@ -212,11 +209,94 @@ def ecc_evaluate(ctx: Context, P, sino, W: int, H: int, n_kappa: int, cauchy_c: 
             nkappa = torch.empty((n_pairs,), dtype=torch.int32, device=dev)
         _dev(per_pair, torch.float64, "per_pair", (n_pairs, 2))
         _dev(nkappa, torch.int32, "nkappa", (n_pairs,))
-    rc = load().ecc_evaluate(ctx.handle, N, _ptr(P), _ptr(motion), _ptr(sino), _ptr(scales), int(W), int(H), n_alpha,
-                             n_s, code, int(n_kappa), float(cauchy_c), _ptr(pairs), int(n_pairs), _ptr(total),
-                             _ptr(per_pair), _ptr(nkappa), _stream(stream))
+    return code, N, P, sino, motion, pairs, n_pairs, scales, total, per_pair, nkappa
+
+
+def ecc_evaluate(ctx: Context, P, sino, W: int, H: int, n_kappa: int, cauchy_c: float = 0.0, motion=None,
+                 pairs=None, scales=None, total=None, per_pair=None, nkappa=None, want_per_pair: bool = True,
+                 stream=None) -> dict:
+    """Consistency over pairs (all a < b if pairs is None).  Returns CUDA tensors
+    total [1] float64, per_pair [n_pairs, 2] float64 (d, e) and nkappa [n_pairs] int32."""
+    code, N, P, sino, motion, pairs, n_pairs, scales, total, per_pair, nkappa = _eval_args(
+        P, sino, motion, pairs, scales, total, per_pair, nkappa, want_per_pair)
+    rc = load().ecc_evaluate(ctx.handle, N, _ptr(P), _ptr(motion), _ptr(sino), _ptr(scales), int(W), int(H),
+                             sino.shape[1], sino.shape[2], code, int(n_kappa), float(cauchy_c), _ptr(pairs),
+                             int(n_pairs), _ptr(total), _ptr(per_pair), _ptr(nkappa), _stream(stream))
     _check(ctx, rc, "ecc_evaluate")
     return {"total": total, "per_pair": per_pair, "nkappa": nkappa}
+
+
+def ecc_evaluate_frozen(ctx: Context, P, sino, W: int, H: int, n_kappa: int, cauchy_c: float = 0.0, motion=None,
+                        pairs=None, scales=None, total=None, per_pair=None, nkappa=None,
+                        want_per_pair: bool = True, stream=None) -> dict:
+    """As ecc_evaluate with the planes sampled by the previous call on ctx (for
+    finite-difference checks of the gradient); pass the same pairs tensor."""
+    code, N, P, sino, motion, pairs, n_pairs, scales, total, per_pair, nkappa = _eval_args(
+        P, sino, motion, pairs, scales, total, per_pair, nkappa, want_per_pair)
+    rc = load().ecc_evaluate_frozen(ctx.handle, N, _ptr(P), _ptr(motion), _ptr(sino), _ptr(scales), int(W), int(H),
+                                    sino.shape[1], sino.shape[2], code, int(n_kappa), float(cauchy_c), _ptr(pairs),
+                                    int(n_pairs), _ptr(total), _ptr(per_pair), _ptr(nkappa), _stream(stream))
+    _check(ctx, rc, "ecc_evaluate_frozen")
+    return {"total": total, "per_pair": per_pair, "nkappa": nkappa}
+
+
+def ecc_evaluate_grad(ctx: Context, P, sino, W: int, H: int, n_kappa: int, cauchy_c: float = 0.0, motion=None,
+                      pairs=None, scales=None, total=None, per_pair=None, nkappa=None, grad=None,
+                      want_per_pair: bool = True, stream=None) -> dict:
+    """As ecc_evaluate plus grad [N, 6] float64 = d total / d motion (sampled planes
+    held at the evaluation point)."""
+    torch = _torch()
+    code, N, P, sino, motion, pairs, n_pairs, scales, total, per_pair, nkappa = _eval_args(
+        P, sino, motion, pairs, scales, total, per_pair, nkappa, want_per_pair)
+    if grad is None:
+        grad = torch.empty((N, 6), dtype=torch.float64, device=sino.device)
+    _dev(grad, torch.float64, "grad", (N, 6))
+    rc = load().ecc_evaluate_grad(ctx.handle, N, _ptr(P), _ptr(motion), _ptr(sino), _ptr(scales), int(W), int(H),
+                                  sino.shape[1], sino.shape[2], code, int(n_kappa), float(cauchy_c), _ptr(pairs),
+                                  int(n_pairs), _ptr(total), _ptr(per_pair), _ptr(nkappa), _ptr(grad),
+                                  _stream(stream))
+    _check(ctx, rc, "ecc_evaluate_grad")
+    return {"total": total, "per_pair": per_pair, "nkappa": nkappa, "grad": grad}
+
+
+def _autograd_function():
+    torch = _torch()
+
+    class _Consistency(torch.autograd.Function):
+        """total(motion) with the adjoint kernel as backward."""
+
+        @staticmethod
+        def forward(fctx, motion, ctx, P, sino, W, H, n_kappa, cauchy_c, pairs, scales):
+            motion = motion.detach().contiguous()
+            if motion.requires_grad or fctx.needs_input_grad[0]:
+                r = ecc_evaluate_grad(ctx, P, sino, W, H, n_kappa, cauchy_c, motion=motion, pairs=pairs,
+                                      scales=scales, want_per_pair=False)
+                fctx.save_for_backward(r["grad"])
+            else:
+                r = ecc_evaluate(ctx, P, sino, W, H, n_kappa, cauchy_c, motion=motion, pairs=pairs, scales=scales,
+                                 want_per_pair=False)
+                fctx.save_for_backward(torch.zeros_like(motion))
+            return r["total"][0].clone()
+
+        @staticmethod
+        def backward(fctx, g):
+            (grad,) = fctx.saved_tensors
+            return (g * grad, None, None, None, None, None, None, None, None, None)
+
+    return _Consistency
+
+
+_FN = None
+
+
+def consistency(ctx: Context, motion, P, sino, W: int, H: int, n_kappa: int, cauchy_c: float = 0.0, pairs=None,
+                scales=None):
+    """Differentiable total (Eq. 17) as a function of the per-view motion [N, 6]
+    (torch.autograd.Function; backward = the library's adjoint kernel)."""
+    global _FN
+    if _FN is None:
+        _FN = _autograd_function()
+    return _FN.apply(motion, ctx, P, sino, W, H, n_kappa, cauchy_c, pairs, scales)
 
 
 def ecc_scan_consistency_host(ctx: Context, P, images, n_alpha: int, n_s: int, n_kappa: int,

@@ -40,7 +40,12 @@ struct ecc_ctx {
   size_t held = 0;
   std::string err;
   int* d_status = nullptr;
-  Buf views, pairs, ctile, adir, perpair, nk, partial, rtable, wimg;
+  Buf views, pairs, ctile, adir, perpair, nk, partial, rtable, wimg, stage;
+  Buf vtan, Gpp, gpp;  // adjoint scratch
+  // sampling of the last evaluation (for ecc_evaluate_frozen)
+  bool samp_valid = false;
+  int samp_views = 0, samp_pairs = 0, samp_K = 0, samp_W = 0, samp_H = 0;
+  const void* samp_pair_ptr = nullptr;
   Buf h_P, h_img, h_sino, h_total;  // buffers of the host-buffer entry point
 };
 
@@ -148,10 +153,6 @@ int check_geometry_args(ecc_ctx* c, int n_views, const void* P, int W, int H, in
   return ECC_OK;
 }
 
-__global__ void fill_kernel(float* p, int n, float v) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) p[i] = v;
-}
 
 int run_precompute(ecc_ctx* c, int n_views, const double* P, const float* images, int W, int H, int n_alpha, int n_s,
                    int dtype, void* sino_out, float* scales_out, cudaStream_t s) {
@@ -159,10 +160,13 @@ int run_precompute(ecc_ctx* c, int n_views, const double* P, const float* images
   if ((rc = ensure(c, c->views, sizeof(ecc::ViewRec) * (size_t)n_views, "views")) != ECC_OK) return rc;
   const size_t tbytes = sizeof(ecc::RadonRow) * (size_t)n_views * n_alpha + sizeof(ecc::RadonView) * (size_t)n_views;
   if ((rc = ensure(c, c->rtable, tbytes, "radon table")) != ECC_OK) return rc;
-  const size_t plane = (size_t)H * (W + 4) + (size_t)W * (H + 4);
+  const size_t plane = ecc::radon_plane_floats(W, H, n_s);
   const size_t max_batch_bytes = (size_t)256 << 20;
   int batch = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_views, max_batch_bytes / (plane * 4)));
   if ((rc = ensure(c, c->wimg, plane * 4 * (size_t)batch, "weighted images")) != ECC_OK) return rc;
+  if (dtype == ECC_F16 &&
+      (rc = ensure(c, c->stage, ecc::radon_f16_stage_bytes(n_alpha, n_s, batch), "FP16 staging")) != ECC_OK)
+    return rc;
   const ecc::LaunchHooks hk = hooks_of(c);
   hk.on_begin("view_setup_kernel", s);
   ecc::view_setup_kernel<<<(n_views + 127) / 128, 128, 0, s>>>(n_views, P, nullptr, W, H, (ecc::ViewRec*)c->views.p,
@@ -171,23 +175,24 @@ int run_precompute(ecc_ctx* c, int n_views, const double* P, const float* images
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "view set-up launch");
   e = ecc::launch_radon((const ecc::ViewRec*)c->views.p, n_views, images, W, H, n_alpha, n_s, dtype, sino_out,
-                        scales_out, (ecc::RadonRow*)c->rtable.p, (float*)c->wimg.p, batch, hk, s);
+                        scales_out, (ecc::RadonRow*)c->rtable.p, (float*)c->wimg.p, (float*)c->stage.p, batch, hk, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "radon launch");
-  if (dtype == ECC_F16 && scales_out) {
-    hk.on_begin("fill_kernel", s);
-    fill_kernel<<<(n_views + 255) / 256, 256, 0, s>>>(scales_out, n_views, 1.0f);
-    hk.on_end("fill_kernel", s);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "scale fill launch");
-  }
   return ECC_OK;
 }
 
 int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion, const void* sino,
                  const float* scales, int W, int H, int n_alpha, int n_s, int dtype, int n_kappa, double cauchy_c,
-                 const int32_t* pairs, int n_pairs, double* total, double* per_pair, int32_t* nkappa,
-                 cudaStream_t s) {
+                 const int32_t* pairs, int n_pairs, double* total, double* per_pair, int32_t* nkappa, double* grad,
+                 bool reuse, cudaStream_t s) {
   int rc;
   cudaError_t e;
+  if (reuse && !(c->samp_valid && c->samp_views == n_views && c->samp_pairs == n_pairs && c->samp_K == n_kappa &&
+                 c->samp_W == W && c->samp_H == H && c->samp_pair_ptr == (const void*)pairs))
+    return fail(c, ECC_EINVAL, "no previous evaluation on this context with the same views, pairs and n_kappa");
+  if (grad && n_pairs == 0) {
+    e = cudaMemsetAsync(grad, 0, sizeof(double) * 6 * (size_t)n_views, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "memset grad");
+  }
   if (n_pairs == 0) {
     e = cudaMemsetAsync(total, 0, sizeof(double), s);
     return e == cudaSuccess ? ECC_OK : cuda_fail(c, e, "memset total");
@@ -204,6 +209,12 @@ int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion,
     if ((rc = ensure(c, c->perpair, sizeof(double) * 2 * (size_t)np, "per-pair")) != ECC_OK) return rc;
     per_pair = (double*)c->perpair.p;
   }
+  if (grad) {
+    if ((rc = ensure(c, c->vtan, sizeof(ecc::ViewTan) * (size_t)n_views, "view tangents")) != ECC_OK) return rc;
+    if ((rc = ensure(c, c->Gpp, sizeof(double) * 12 * (size_t)np, "pair adjoints")) != ECC_OK) return rc;
+    if ((rc = ensure(c, c->gpp, sizeof(double) * 12 * (size_t)np, "pair gradients")) != ECC_OK) return rc;
+  }
+  if (!reuse) c->samp_valid = false;
   const ecc::LaunchHooks hk = hooks_of(c);
   hk.on_begin("view_setup_kernel", s);
   ecc::view_setup_kernel<<<(n_views + 127) / 128, 128, 0, s>>>(n_views, P, motion, W, H, (ecc::ViewRec*)c->views.p,
@@ -217,17 +228,45 @@ int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion,
   hk.on_begin("pair_setup_kernel", s);
   ecc::pair_setup_kernel<<<(unsigned)((np + 127) / 128), 128, 0, s>>>(
       n_views, np, pairs, (const ecc::ViewRec*)c->views.p, W, H, n_kappa, (ecc::PairRec*)c->pairs.p,
-      (double2*)c->ctile.p, n_tiles, c->d_status);
+      (double2*)c->ctile.p, n_tiles, reuse ? 1 : 0, c->d_status);
   hk.on_end("pair_setup_kernel", s);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "pair set-up launch");
   const double inv_ds = (double)(n_s - 1) / std::sqrt((double)W * W + (double)H * H);
   int nb = 0;
   e = ecc::launch_ecc_pairs(np, (const ecc::PairRec*)c->pairs.p, (const double2*)c->ctile.p, n_tiles,
                             (const double2*)c->adir.p, sino, scales, dtype, n_alpha, n_s, n_kappa, inv_ds, cauchy_c,
-                            per_pair, nkappa, (double*)c->partial.p, &nb, hk, s);
+                            per_pair, nkappa, (double*)c->partial.p, grad ? (double*)c->Gpp.p : nullptr, &nb, hk,
+                            s);
   if (e != cudaSuccess) return cuda_fail(c, e, "pair kernel launch");
   e = ecc::launch_reduce((const double*)c->partial.p, nb, total, hk, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "reduce launch");
+  if (grad) {
+    hk.on_begin("view_tangent_kernel", s);
+    ecc::view_tangent_kernel<<<(n_views + 63) / 64, 64, 0, s>>>(n_views, P, motion, W, H,
+                                                               (ecc::ViewTan*)c->vtan.p);
+    hk.on_end("view_tangent_kernel", s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "view tangent launch");
+    hk.on_begin("pair_grad_kernel", s);
+    ecc::pair_grad_kernel<<<(unsigned)((np + 63) / 64), 64, 0, s>>>(np, (const ecc::PairRec*)c->pairs.p,
+                                                                    (const ecc::ViewRec*)c->views.p,
+                                                                    (const ecc::ViewTan*)c->vtan.p,
+                                                                    (const double*)c->Gpp.p, (double*)c->gpp.p);
+    hk.on_end("pair_grad_kernel", s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "pair gradient launch");
+    hk.on_begin("view_grad_reduce_kernel", s);
+    ecc::view_grad_reduce_kernel<<<n_views, 256, 0, s>>>(n_views, np, pairs, (const double*)c->gpp.p, grad);
+    hk.on_end("view_grad_reduce_kernel", s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "gradient reduce launch");
+  }
+  if (!reuse) {
+    c->samp_valid = true;
+    c->samp_views = n_views;
+    c->samp_pairs = n_pairs;
+    c->samp_K = n_kappa;
+    c->samp_W = W;
+    c->samp_H = H;
+    c->samp_pair_ptr = pairs;
+  }
   return ECC_OK;
 }
 
@@ -267,7 +306,7 @@ void ecc_destroy(ecc_ctx* c) {
   DeviceGuard g(c->device);
   cudaDeviceSynchronize();
   Buf* bufs[] = {&c->views, &c->pairs, &c->ctile, &c->adir, &c->perpair, &c->nk, &c->partial, &c->rtable, &c->wimg,
-                 &c->h_P, &c->h_img, &c->h_sino, &c->h_total};
+                 &c->vtan, &c->Gpp, &c->gpp, &c->stage, &c->h_P, &c->h_img, &c->h_sino, &c->h_total};
   for (Buf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->d_status) cudaFree(c->d_status);
@@ -354,9 +393,10 @@ int ecc_precompute_radon_derivative(ecc_ctx* c, int n_views, const double* P, co
                         (cudaStream_t)stream);
 }
 
-int ecc_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion, const void* sino,
-                 const float* scales, int W, int H, int n_alpha, int n_s, int dtype, int n_kappa, double cauchy_c,
-                 const int32_t* pairs, int n_pairs, double* total, double* per_pair, int32_t* nkappa, void* stream) {
+namespace {
+int check_eval_args(ecc_ctx* c, int n_views, const double* P, const void* sino, const float* scales, int W, int H,
+                    int n_alpha, int n_s, int dtype, int n_kappa, double cauchy_c, const int32_t* pairs, int n_pairs,
+                    const double* total) {
   if (!c) return fail(nullptr, ECC_EINVAL, "ctx is NULL");
   int rc = check_geometry_args(c, n_views, P, W, H, n_alpha, n_s, dtype);
   if (rc != ECC_OK) return rc;
@@ -364,15 +404,50 @@ int ecc_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion,
   if (dtype == ECC_F16 && !scales) return fail(c, ECC_EINVAL, "ECC_F16 needs scales");
   if (n_kappa < 1 || n_kappa > 65536) return fail(c, ECC_EINVAL, "n_kappa %d out of range [1, 65536]", n_kappa);
   if (n_pairs < 0) return fail(c, ECC_EINVAL, "n_pairs %d < 0", n_pairs);
-  if (!pairs) {
+  if (!pairs && n_pairs > 0) {
     const long long all = (long long)n_views * (n_views - 1) / 2;
     if (all != n_pairs)
       return fail(c, ECC_EINVAL, "pairs is NULL but n_pairs (%d) != n_views (n_views - 1) / 2 (%lld)", n_pairs, all);
   }
   if (!std::isfinite(cauchy_c)) return fail(c, ECC_EINVAL, "cauchy_c is not finite");
+  return ECC_OK;
+}
+}  // namespace
+
+int ecc_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion, const void* sino,
+                 const float* scales, int W, int H, int n_alpha, int n_s, int dtype, int n_kappa, double cauchy_c,
+                 const int32_t* pairs, int n_pairs, double* total, double* per_pair, int32_t* nkappa, void* stream) {
+  int rc = check_eval_args(c, n_views, P, sino, scales, W, H, n_alpha, n_s, dtype, n_kappa, cauchy_c, pairs, n_pairs,
+                           total);
+  if (rc != ECC_OK) return rc;
   DeviceGuard g(c->device);
   return run_evaluate(c, n_views, P, motion, sino, scales, W, H, n_alpha, n_s, dtype, n_kappa, cauchy_c, pairs,
-                      n_pairs, total, per_pair, nkappa, (cudaStream_t)stream);
+                      n_pairs, total, per_pair, nkappa, nullptr, false, (cudaStream_t)stream);
+}
+
+int ecc_evaluate_frozen(ecc_ctx* c, int n_views, const double* P, const double* motion, const void* sino,
+                        const float* scales, int W, int H, int n_alpha, int n_s, int dtype, int n_kappa,
+                        double cauchy_c, const int32_t* pairs, int n_pairs, double* total, double* per_pair,
+                        int32_t* nkappa, void* stream) {
+  int rc = check_eval_args(c, n_views, P, sino, scales, W, H, n_alpha, n_s, dtype, n_kappa, cauchy_c, pairs, n_pairs,
+                           total);
+  if (rc != ECC_OK) return rc;
+  DeviceGuard g(c->device);
+  return run_evaluate(c, n_views, P, motion, sino, scales, W, H, n_alpha, n_s, dtype, n_kappa, cauchy_c, pairs,
+                      n_pairs, total, per_pair, nkappa, nullptr, true, (cudaStream_t)stream);
+}
+
+int ecc_evaluate_grad(ecc_ctx* c, int n_views, const double* P, const double* motion, const void* sino,
+                      const float* scales, int W, int H, int n_alpha, int n_s, int dtype, int n_kappa,
+                      double cauchy_c, const int32_t* pairs, int n_pairs, double* total, double* per_pair,
+                      int32_t* nkappa, double* grad, void* stream) {
+  int rc = check_eval_args(c, n_views, P, sino, scales, W, H, n_alpha, n_s, dtype, n_kappa, cauchy_c, pairs, n_pairs,
+                           total);
+  if (rc != ECC_OK) return rc;
+  if (!grad) return fail(c, ECC_EINVAL, "grad is NULL");
+  DeviceGuard g(c->device);
+  return run_evaluate(c, n_views, P, motion, sino, scales, W, H, n_alpha, n_s, dtype, n_kappa, cauchy_c, pairs,
+                      n_pairs, total, per_pair, nkappa, grad, false, (cudaStream_t)stream);
 }
 
 int ecc_scan_consistency_host(ecc_ctx* c, int n_views, const double* P_host, const float* images_host, int W,
@@ -402,7 +477,7 @@ int ecc_scan_consistency_host(ecc_ctx* c, int n_views, const double* P_host, con
                       c->h_sino.p, nullptr, s);
   if (rc != ECC_OK) return rc;
   rc = run_evaluate(c, n_views, (const double*)c->h_P.p, nullptr, c->h_sino.p, nullptr, W, H, n_alpha, n_s, ECC_F32,
-                    n_kappa, cauchy_c, nullptr, (int)np, (double*)c->h_total.p, nullptr, nullptr, s);
+                    n_kappa, cauchy_c, nullptr, (int)np, (double*)c->h_total.p, nullptr, nullptr, nullptr, false, s);
   if (rc != ECC_OK) return rc;
   e = cudaMemcpyAsync(total_host, c->h_total.p, sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -411,3 +486,24 @@ int ecc_scan_consistency_host(ecc_ctx* c, int n_views, const double* P_host, con
 }
 
 }  // extern "C"
+
+// Internal (tests and diagnostics only, not part of the public ABI): copies the
+// first n view records and pair records of the last evaluation to host memory.
+extern "C" int ecc_internal_dump(ecc_ctx* c, void* stream, int n_views, int n_pairs, void* views_out,
+                                 void* pairs_out) {
+  if (!c) return ECC_EINVAL;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && n_views > 0 && views_out && c->views.p)
+    e = cudaMemcpy(views_out, c->views.p, sizeof(ecc::ViewRec) * (size_t)n_views, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && n_pairs > 0 && pairs_out && c->pairs.p)
+    e = cudaMemcpy(pairs_out, c->pairs.p, sizeof(ecc::PairRec) * (size_t)n_pairs, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? ECC_OK : cuda_fail(c, e, "dump");
+}
+
+extern "C" int ecc_internal_record_sizes(int* view_bytes, int* pair_bytes) {
+  *view_bytes = (int)sizeof(ecc::ViewRec);
+  *pair_bytes = (int)sizeof(ecc::PairRec);
+  return 0;
+}

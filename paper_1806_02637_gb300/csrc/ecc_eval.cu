@@ -69,6 +69,7 @@ struct Anchor {
   float a, b;      // rate of the normal direction in the anchor frame
   float p3, s0;    // rate of the offset, anchor offset s [px]
   float sg;        // orientation fold of the anchor (+1 / -1)
+  float gh, gl;    // exact s-index advance per sample step: gh (17 significant bits) + gl
 };
 
 __device__ __forceinline__ Anchor shfl_anchor(const Anchor& x, int src) {
@@ -82,6 +83,8 @@ __device__ __forceinline__ Anchor shfl_anchor(const Anchor& x, int src) {
   r.p3 = __shfl_sync(0xffffffffu, x.p3, src);
   r.s0 = __shfl_sync(0xffffffffu, x.s0, src);
   r.sg = __shfl_sync(0xffffffffu, x.sg, src);
+  r.gh = __shfl_sync(0xffffffffu, x.gh, src);
+  r.gl = __shfl_sync(0xffffffffu, x.gl, src);
   return r;
 }
 
@@ -89,28 +92,30 @@ __device__ __forceinline__ Anchor shfl_anchor(const Anchor& x, int src) {
 // coordinates) of the tile-centre plane, folded to alpha in [0, pi), located on
 // the alpha grid against the exact row direction, and its s offset.
 __device__ Anchor make_anchor(const double* __restrict__ A, double2 c, const double2* __restrict__ alpha_dir,
-                              int n_alpha, float inv_dalpha, double inv_ds, double half_ns1, float inv_ds_f) {
+                              int n_alpha, float inv_dalpha, double inv_ds, double half_ns1, float inv_ds_f,
+                              double dk) {
   double l0 = A[0] * c.x + A[1] * c.y;
   double l1 = A[2] * c.x + A[3] * c.y;
   double l2 = A[4] * c.x + A[5] * c.y;
-  const float cpx = (float)(-c.y), cpy = (float)c.x;  // c rotated by +90 degrees
-  float q0 = (float)A[0] * cpx + (float)A[1] * cpy;
-  float q1 = (float)A[2] * cpx + (float)A[3] * cpy;
-  float q2 = (float)A[4] * cpx + (float)A[5] * cpy;
+  // derivative of the line with respect to kappa: A c_perp, c_perp = (-c.y, c.x)
+  double p0 = A[1] * c.x - A[0] * c.y;
+  double p1 = A[3] * c.x - A[2] * c.y;
+  double p2 = A[5] * c.x - A[4] * c.y;
   Anchor r;
   r.sg = 1.0f;
   if (l1 < 0.0 || (l1 == 0.0 && l0 < 0.0)) {
     l0 = -l0; l1 = -l1; l2 = -l2;
-    q0 = -q0; q1 = -q1; q2 = -q2;
+    p0 = -p0; p1 = -p1; p2 = -p2;
     r.sg = -1.0f;
   }
   const float l0f = (float)l0, l1f = (float)l1;
+  const float q0 = (float)p0, q1 = (float)p1, q2 = (float)p2;
   const float h = sqrtf(l0f * l0f + l1f * l1f);
-  const float ih = 1.0f / h;
-  const float chx = l0f * ih, chy = l1f * ih;
-  r.a = (q0 * chx + q1 * chy) * ih;
-  r.b = (q1 * chx - q0 * chy) * ih;
-  r.p3 = q2 * ih;
+  const float ih_f = 1.0f / h;
+  const float chx = l0f * ih_f, chy = l1f * ih_f;
+  r.a = (q0 * chx + q1 * chy) * ih_f;
+  r.b = (q1 * chx - q0 * chy) * ih_f;
+  r.p3 = q2 * ih_f;
   int m = (int)floorf(atan2f(l1f, l0f) * inv_dalpha);
   m = m < 0 ? 0 : (m > n_alpha - 1 ? n_alpha - 1 : m);
   const double2 u = alpha_dir[m];
@@ -130,49 +135,139 @@ __device__ Anchor make_anchor(const double* __restrict__ A, double2 c, const dou
   r.n0 = (int)nf;
   r.fs0 = (float)(is - nf) - sigf * 2.0f * sh * sh * inv_ds_f;
   r.s0 = sigf * cosf(th);
+  // exact first-order advance of the s index per sample: (ds/dkappa) dk / ds_bin in
+  // FP64, ds/dkappa = (1/h) (-l2' + l2 (l . l') / h^2), 1/h = cos(th) / dt
+  const double thd = (double)th;
+  const double ihd = rr * (1.0 - 0.5 * thd * thd * (1.0 - thd * thd * (1.0 / 12.0)));
+  const double t1 = l0 * p0 + l1 * p1;
+  const double g = ihd * (-p2 + l2 * t1 * ihd * ihd) * dk * inv_ds;
+  const float gh = __int_as_float(__float_as_int((float)g) & (int)0xffffffc0);
+  r.gh = gh;
+  r.gl = (float)(g - (double)gh);
   return r;
 }
 
-// One sample of one view: move from the anchor by delta = (lane - 15.5) dk
-// (x, y: the normal direction in the anchor frame; r = |(x, y)|), fold, gather.
-template <typename T>
-__device__ __forceinline__ float sample(const T* __restrict__ sv, int n_alpha, int n_s, const Anchor& an, float cd,
-                                        float sd, float inv_dalpha, float inv_ds_f) {
+// Position of one sample of one view in the sinogram grid, moving from the tile
+// anchor by delta = jj dk (jj a half-integer lane offset; sd, cd = sin, cos delta).
+// alpha: the normal turns by atan2(b sd, cd + a sd) in the anchor frame.  s: the
+// first-order part jj * (gh + gl) is exact (gh * jj is exact in FP32, its integer
+// part split off exactly), and the remainder, of second order in delta, is
+// evaluated in a cancellation-free form:
+//   ds - G1 delta = -(s0 q + p3) u - s0 (q - a) delta,
+//   u = sd/r - delta = ((sin delta - delta) - delta (r - 1)) / r,
+//   r^2 - 1 = sd (2 a cd + (a^2 + b^2 - 1) sd),  q = (2 a cd + (a^2 + b^2) sd)/(cd + r).
+struct Loc {
+  int m, n;
+  float fa, fs, sign;
+  bool ok;
+};
+
+__device__ __forceinline__ Loc locate(const Anchor& an, float cd, float sd, float jj, float de, int n_alpha,
+                                      int n_s, float inv_dalpha, float inv_ds_f) {
   const float x = fmaf(an.a, sd, cd);
   const float y = an.b * sd;
   const float dal = atan2f(y, x);
-  const float r = sqrtf(fmaf(x, x, y * y));
   const float ab2 = fmaf(an.a, an.a, an.b * an.b);
-  const float q = __fdividef(fmaf(2.0f * an.a, cd, ab2 * sd), cd + r);
-  const float dls = -sd * __fdividef(fmaf(an.s0, q, an.p3), r);
+  const float r2m1 = sd * fmaf(2.0f * an.a, cd, (ab2 - 1.0f) * sd);
+  const float r = sqrtf(1.0f + r2m1);
+  const float rm1 = __fdividef(r2m1, r + 1.0f);
+  const float cpr = cd + r;
+  const float q = __fdividef(fmaf(2.0f * an.a, cd, ab2 * sd), cpr);
+  const float qma = sd * __fdividef(fmaf(-an.a, q, ab2), cpr);
+  const float d2 = de * de;
+  // sin(delta) - delta by its Taylor series to delta^13 (relative truncation below
+  // 4e-8 for |delta| <= 1.5, the widest tile of a full-pi arc with K >= 32)
+  float sdmd = fmaf(d2, 1.0f / 6227020800.0f, -1.0f / 39916800.0f);
+  sdmd = fmaf(d2, sdmd, 1.0f / 362880.0f);
+  sdmd = fmaf(d2, sdmd, -1.0f / 5040.0f);
+  sdmd = fmaf(d2, sdmd, 1.0f / 120.0f);
+  sdmd = fmaf(d2, sdmd, -1.0f / 6.0f);
+  sdmd *= de * d2;
+  const float u = __fdividef(fmaf(-de, rm1, sdmd), r);
+  const float R = -fmaf(an.s0, q, an.p3) * u - an.s0 * qma * de;
+  const float lin = an.gh * jj;  // exact
+  const float Li = floorf(lin);
+  const float Lf = lin - Li;     // exact
   float fa = fmaf(dal, inv_dalpha, an.fa0);
-  float fs = fmaf(dls, inv_ds_f, an.fs0);
+  float fs = (an.fs0 + Lf) + fmaf(an.gl, jj, R * inv_ds_f);
   // masked samples of the other view may carry extreme offsets: clamp before the
   // integer conversion so that no index arithmetic can overflow
   const float mfl = fminf(fmaxf(floorf(fa), -4.0e6f), 4.0e6f);
   const float nfl = fminf(fmaxf(floorf(fs), -4.0e6f), 4.0e6f);
-  int m = an.m0 + (int)mfl;
-  int n = an.n0 + (int)nfl;
-  fa -= mfl;
-  fs -= nfl;
-  float sign = an.sg;
-  if (m >= n_alpha || m < 0) {  // alpha left [0, pi): S(alpha + pi, s) = -S(alpha, -s)
-    m += m < 0 ? n_alpha : -n_alpha;
-    n = n_s - 2 - n;
-    fs = 1.0f - fs;
-    sign = -sign;
+  const float lif = fminf(fmaxf(Li, -4.0e6f), 4.0e6f);
+  Loc o;
+  o.m = an.m0 + (int)mfl;
+  o.n = an.n0 + (int)lif + (int)nfl;
+  o.fa = fa - mfl;
+  o.fs = fs - nfl;
+  o.sign = an.sg;
+  if (o.m >= n_alpha || o.m < 0) {  // alpha left [0, pi): S(alpha + pi, s) = -S(alpha, -s)
+    o.m += o.m < 0 ? n_alpha : -n_alpha;
+    o.n = n_s - 2 - o.n;
+    o.fs = 1.0f - o.fs;
+    o.sign = -o.sign;
   }
-  if (m < 0 || m >= n_alpha) return 0.0f;  // only reachable for a masked sample
-  return sign * bilinear(sv, n_alpha, n_s, m, fa, n, fs);
+  o.ok = o.m >= 0 && o.m < n_alpha;  // false only for a masked sample
+  return o;
 }
 
+// One sample of one view: locate it and gather the bilinear value.
 template <typename T>
+__device__ __forceinline__ float sample(const T* __restrict__ sv, int n_alpha, int n_s, const Anchor& an, float cd,
+                                        float sd, float jj, float de, float inv_dalpha, float inv_ds_f) {
+  const Loc o = locate(an, cd, sd, jj, de, n_alpha, n_s, inv_dalpha, inv_ds_f);
+  if (!o.ok) return 0.0f;
+  return o.sign * bilinear(sv, n_alpha, n_s, o.m, o.fa, o.n, o.fs);
+}
+
+// Value and gradient of one sample with respect to its line l = A c (centred
+// detector coordinates) for the adjoint.  The look-up is evaluated at the folded
+// line L = sigma l (sigma = product of the orientation folds, the same sign that
+// multiplies the value), so dS/dl = B_alpha d(alpha)/dL + B_s d(s)/dL at L with
+// d(alpha)/dL = (-sin a, cos a, 0)/h and d(s)/dL = -(s cos a, s sin a, 1)/h;
+// B_alpha, B_s are the slopes of the bilinear cell (piecewise constant).
+template <typename T>
+__device__ __forceinline__ float sample_grad(const T* __restrict__ sv, int n_alpha, int n_s, const Anchor& an,
+                                             float cd, float sd, float jj, float de, float inv_dalpha,
+                                             float inv_ds_f, float l0, float l1, float l2, float scale, float* g) {
+  const Loc o = locate(an, cd, sd, jj, de, n_alpha, n_s, inv_dalpha, inv_ds_f);
+  const int m = o.m, n = o.n;
+  const float fa = o.fa, fs = o.fs, sign = o.sign;
+  g[0] = g[1] = g[2] = 0.0f;
+  if (!o.ok) return 0.0f;
+  const T* r0 = sv + (size_t)m * n_s;
+  const float t00 = fetch(r0, n, n_s), t01 = fetch(r0, n + 1, n_s);
+  const float v0 = fmaf(fs, t01 - t00, t00);
+  const float dv0 = t01 - t00;
+  float v1, dv1;
+  if (m + 1 < n_alpha) {
+    const T* r1 = r0 + n_s;
+    const float t10 = fetch(r1, n, n_s), t11 = fetch(r1, n + 1, n_s);
+    v1 = fmaf(fs, t11 - t10, t10);
+    dv1 = t11 - t10;
+  } else {
+    const float t10 = fetch(sv, n_s - 1 - n, n_s), t11 = fetch(sv, n_s - 2 - n, n_s);
+    v1 = -fmaf(fs, t11 - t10, t10);
+    dv1 = -(t11 - t10);
+  }
+  const float Ba = (v1 - v0) * inv_dalpha * scale;
+  const float Bs = fmaf(fa, dv1 - dv0, dv0) * inv_ds_f * scale;
+  const float L0 = sign * l0, L1 = sign * l1, L2 = sign * l2;
+  const float ih = rsqrtf(fmaf(L0, L0, L1 * L1));
+  const float ca = L0 * ih, sa = L1 * ih, sf = -L2 * ih;
+  g[0] = ih * (-Ba * sa - Bs * sf * ca);
+  g[1] = ih * (Ba * ca - Bs * sf * sa);
+  g[2] = -ih * Bs;
+  return scale * sign * fmaf(fa, v1 - v0, v0);
+}
+
+template <typename T, bool GRAD>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     ecc_pair_kernel(long long n_pairs, const PairRec* __restrict__ prs, const double2* __restrict__ ctile,
                     int n_tiles, const double2* __restrict__ alpha_dir, const T* __restrict__ sino,
                     const float* __restrict__ scales, int n_alpha, int n_s, int K, double inv_ds,
                     float cauchy_c, double* __restrict__ per_pair, int32_t* __restrict__ nk_out,
-                    double* __restrict__ block_partial) {
+                    double* __restrict__ block_partial, double* __restrict__ Gpp) {
   __shared__ double e_warp[kWarpsPerBlock];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -183,6 +278,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     const int status = pr.status;
     const int nk = status == 0 ? pr.nk : 0;
     float acc = 0.0f;
+    float G[12];  // adjoint only: sum_k 2 (S_a - S_b) (dS/dl) c_k^T for views a (0..5), b (6..11)
+#pragma unroll
+    for (int i = 0; i < 12; ++i) G[i] = 0.0f;
     if (nk > 0) {
       const size_t vstride = (size_t)n_alpha * n_s;
       const T* sa = sino + (size_t)pr.a * vstride;
@@ -192,17 +290,29 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       const float inv_dalpha = (float)((double)n_alpha / kPi);
       const double half_ns1 = 0.5 * (n_s - 1);
       const float inv_ds_f = (float)inv_ds;
-      float sd, cd;
-      sincosf(((float)lane - 15.5f) * (float)pr.dk, &sd, &cd);
+      // offset of this lane's plane from its tile centre: (j + 1/2 - n_t/2) dk for a
+      // tile of n_t samples (n_t = 32 except for the last tile)
+      const float dkf = (float)pr.dk;
+      const float jj_full = (float)lane - 15.5f;
+      const float jj_last = (float)lane + 0.5f - 0.5f * (float)(K - 32 * (n_tiles - 1));
+      const float de_full = jj_full * dkf, de_last = jj_last * dkf;
+      float sd, cd, sd_last, cd_last;
+      sincosf(de_full, &sd, &cd);
+      sincosf(de_last, &sd_last, &cd_last);
       const int r0lo = pr.r0lo, r0hi = pr.r0hi, r1lo = pr.r1lo, r1hi = pr.r1hi;
       const double2* ct = ctile + p * n_tiles;
+      float Af[12];
+      if (GRAD) {
+#pragma unroll
+        for (int i = 0; i < 12; ++i) Af[i] = (float)(&pr.A[0][0])[i];
+      }
       for (int t0 = 0; t0 < n_tiles; t0 += 16) {
         Anchor mine;
         {
           const int v = lane >> 4;
           int t = t0 + (lane & 15);
           if (t >= n_tiles) t = n_tiles - 1;
-          mine = make_anchor(pr.A[v], ct[t], alpha_dir, n_alpha, inv_dalpha, inv_ds, half_ns1, inv_ds_f);
+          mine = make_anchor(pr.A[v], ct[t], alpha_dir, n_alpha, inv_dalpha, inv_ds, half_ns1, inv_ds_f, pr.dk);
         }
         const int tmax = min(16, n_tiles - t0);
         for (int tt = 0; tt < tmax; ++tt) {
@@ -210,14 +320,46 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
           const Anchor ab = shfl_anchor(mine, 16 + tt);
           const int k = 32 * (t0 + tt) + lane;
           const bool valid = k < K && ((k >= r0lo && k < r0hi) || (k >= r1lo && k < r1hi));
-          const float Sa = sca * sample(sa, n_alpha, n_s, aa, cd, sd, inv_dalpha, inv_ds_f);
-          const float Sb = scb * sample(sb, n_alpha, n_s, ab, cd, sd, inv_dalpha, inv_ds_f);
-          const float dd = Sa - Sb;
-          acc += valid ? dd * dd : 0.0f;
+          const bool last = t0 + tt == n_tiles - 1;
+          const float c_ = last ? cd_last : cd, s_ = last ? sd_last : sd;
+          const float jj = last ? jj_last : jj_full, de = last ? de_last : de_full;
+          if (!GRAD) {
+            const float Sa = sca * sample(sa, n_alpha, n_s, aa, c_, s_, jj, de, inv_dalpha, inv_ds_f);
+            const float Sb = scb * sample(sb, n_alpha, n_s, ab, c_, s_, jj, de, inv_dalpha, inv_ds_f);
+            const float dd = Sa - Sb;
+            acc += valid ? dd * dd : 0.0f;
+          } else {
+            // this lane's plane direction c_k in the (w, v) frame
+            const double2 ctd = ct[t0 + tt];
+            const float cx = (float)ctd.x, cy = (float)ctd.y;
+            const float ckx = cx * c_ - cy * s_, cky = cx * s_ + cy * c_;
+            float ga[3], gb[3];
+            const float Sa = sample_grad(sa, n_alpha, n_s, aa, c_, s_, jj, de, inv_dalpha, inv_ds_f,
+                                         Af[0] * ckx + Af[1] * cky, Af[2] * ckx + Af[3] * cky,
+                                         Af[4] * ckx + Af[5] * cky, sca, ga);
+            const float Sb = sample_grad(sb, n_alpha, n_s, ab, c_, s_, jj, de, inv_dalpha, inv_ds_f,
+                                         Af[6] * ckx + Af[7] * cky, Af[8] * ckx + Af[9] * cky,
+                                         Af[10] * ckx + Af[11] * cky, scb, gb);
+            const float dd = Sa - Sb;
+            acc += valid ? dd * dd : 0.0f;
+            const float w2 = valid ? 2.0f * dd : 0.0f;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+              G[2 * i] = fmaf(w2 * ga[i], ckx, G[2 * i]);
+              G[2 * i + 1] = fmaf(w2 * ga[i], cky, G[2 * i + 1]);
+              G[6 + 2 * i] = fmaf(-w2 * gb[i], ckx, G[6 + 2 * i]);
+              G[6 + 2 * i + 1] = fmaf(-w2 * gb[i], cky, G[6 + 2 * i + 1]);
+            }
+          }
         }
       }
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (GRAD) {
+#pragma unroll
+      for (int i = 0; i < 12; ++i)
+        for (int o = 16; o > 0; o >>= 1) G[i] += __shfl_xor_sync(0xffffffffu, G[i], o);
+    }
     const float d = nk > 0 ? acc / (float)nk : 0.0f;
     const float e = cauchy_c > 0.0f ? d / (1.0f + d / cauchy_c) : d;
     if (lane == 0) {
@@ -226,6 +368,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         per_pair[2 * p + 1] = (double)e;
       }
       if (nk_out) nk_out[p] = nk;
+      if (GRAD) {
+        // d e / d A = (de/dd) (1/N) G
+        const float r = cauchy_c > 0.0f ? 1.0f / (1.0f + d / cauchy_c) : 1.0f;
+        const float scale = nk > 0 ? r * r / (float)nk : 0.0f;
+#pragma unroll
+        for (int i = 0; i < 12; ++i) Gpp[12 * p + i] = (double)(G[i] * scale);
+      }
     }
     e_val = (double)e;
   }
@@ -261,32 +410,39 @@ __global__ void __launch_bounds__(1024) reduce_kernel(const double* __restrict__
 cudaError_t launch_ecc_pairs(long long n_pairs, const PairRec* prs, const double2* ctile, int n_tiles,
                              const double2* alpha_dir, const void* sino, const float* scales, int dtype,
                              int n_alpha, int n_s, int K, double inv_ds, double cauchy_c, double* per_pair,
-                             int32_t* nk_out, double* block_partial, int* n_blocks_out, const LaunchHooks& hooks,
-                             cudaStream_t stream) {
+                             int32_t* nk_out, double* block_partial, double* Gpp, int* n_blocks_out,
+                             const LaunchHooks& hooks, cudaStream_t stream) {
   const long long nb = (n_pairs + kWarpsPerBlock - 1) / kWarpsPerBlock;
   *n_blocks_out = (int)nb;
   if (nb == 0) return cudaSuccess;
   const dim3 grid((unsigned)nb), block(kWarpsPerBlock * 32);
   const float cc = (float)cauchy_c;
-  hooks.on_begin("ecc_pair_kernel", stream);
+  const char* name = Gpp ? "ecc_pair_grad_kernel" : "ecc_pair_kernel";
+  hooks.on_begin(name, stream);
+#define ECC_LAUNCH(TT, SC)                                                                                       \
+  do {                                                                                                         \
+    if (Gpp)                                                                                                   \
+      ecc_pair_kernel<TT, true><<<grid, block, 0, stream>>>(n_pairs, prs, ctile, n_tiles, alpha_dir,            \
+                                                            (const TT*)sino, SC, n_alpha, n_s, K, inv_ds, cc,  \
+                                                            per_pair, nk_out, block_partial, Gpp);             \
+    else                                                                                                       \
+      ecc_pair_kernel<TT, false><<<grid, block, 0, stream>>>(n_pairs, prs, ctile, n_tiles, alpha_dir,           \
+                                                             (const TT*)sino, SC, n_alpha, n_s, K, inv_ds, cc, \
+                                                             per_pair, nk_out, block_partial, nullptr);        \
+  } while (0)
   switch (dtype) {
     case 0:
-      ecc_pair_kernel<float><<<grid, block, 0, stream>>>(n_pairs, prs, ctile, n_tiles, alpha_dir,
-                                                         (const float*)sino, nullptr, n_alpha, n_s, K, inv_ds, cc,
-                                                         per_pair, nk_out, block_partial);
+      ECC_LAUNCH(float, nullptr);
       break;
     case 1:
-      ecc_pair_kernel<__half><<<grid, block, 0, stream>>>(n_pairs, prs, ctile, n_tiles, alpha_dir,
-                                                          (const __half*)sino, scales, n_alpha, n_s, K, inv_ds, cc,
-                                                          per_pair, nk_out, block_partial);
+      ECC_LAUNCH(__half, scales);
       break;
     default:
-      ecc_pair_kernel<__nv_bfloat16><<<grid, block, 0, stream>>>(n_pairs, prs, ctile, n_tiles, alpha_dir,
-                                                                 (const __nv_bfloat16*)sino, nullptr, n_alpha, n_s,
-                                                                 K, inv_ds, cc, per_pair, nk_out, block_partial);
+      ECC_LAUNCH(__nv_bfloat16, nullptr);
       break;
   }
-  hooks.on_end("ecc_pair_kernel", stream);
+#undef ECC_LAUNCH
+  hooks.on_end(name, stream);
   return cudaGetLastError();
 }
 

@@ -27,6 +27,13 @@ struct ViewRec {
   int pad;
 };
 
+// Tangents of the per-view geometry with respect to the view's motion theta (6).
+struct ViewTan {
+  double dC[3][6];
+  double dup[3][6];
+  double dcofc[9][6];
+};
+
 // Per-pair set-up (FP64 geometry, integer sample ranges).
 struct PairRec {
   double A[2][6];   // per view (a, b): l_centred(kappa) = A (cos kappa, sin kappa), 3x2 row-major

@@ -8,6 +8,7 @@
 //                     Eq. 13/14), valid arcs from the detector corners, the sampled
 //                     arc, the integer ranges of valid samples and the direction of
 //                     each 32-sample tile centre.
+#include "dual.cuh"
 #include "ecc_internal.cuh"
 #include "kernels.cuh"
 
@@ -15,98 +16,173 @@ namespace ecc {
 
 namespace {
 
-__device__ inline void cross3(const double* a, const double* b, double* c) {
+template <class T>
+__host__ __device__ inline void cross3(const T* a, const T* b, T* c) {
   c[0] = a[1] * b[2] - a[2] * b[1];
   c[1] = a[2] * b[0] - a[0] * b[2];
   c[2] = a[0] * b[1] - a[1] * b[0];
 }
-__device__ inline double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+template <class T>
+__host__ __device__ inline T dot3(const T* a, const T* b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+__host__ __device__ inline void sc_pair(double x, double* s, double* c) { sincos(x, s, c); }
+template <int N>
+__device__ inline void sc_pair(const Dual<N>& x, Dual<N>* s, Dual<N>* c) { sincos(x, s, c); }
 
 // P T(theta), T = [R t; 0 1], R = Rz(rz) Ry(ry) Rx(rx).
-__device__ void moved_projection(const double* P, const double* th, double* out) {
-  double sx, cx, sy, cy, sz, cz;
-  sincos(th[0], &sx, &cx);
-  sincos(th[1], &sy, &cy);
-  sincos(th[2], &sz, &cz);
-  // R = Rz Ry Rx written out
-  const double R[9] = {cz * cy, cz * sy * sx - sz * cx, cz * sy * cx + sz * sx,
-                       sz * cy, sz * sy * sx + cz * cx, sz * sy * cx - cz * sx,
-                       -sy,     cy * sx,                cy * cx};
+template <class T>
+__host__ __device__ void moved_projection(const double* P, const T* th, T* out) {
+  T sx, cx, sy, cy, sz, cz;
+  sc_pair(th[0], &sx, &cx);
+  sc_pair(th[1], &sy, &cy);
+  sc_pair(th[2], &sz, &cz);
+  const T R[9] = {cz * cy, cz * sy * sx - sz * cx, cz * sy * cx + sz * sx,
+                  sz * cy, sz * sy * sx + cz * cx, sz * sy * cx - cz * sx,
+                  -sy,     cy * sx,                cy * cx};
   for (int i = 0; i < 3; ++i) {
     const double* p = P + 4 * i;
     for (int j = 0; j < 3; ++j) out[4 * i + j] = p[0] * R[j] + p[1] * R[3 + j] + p[2] * R[6 + j];
-    out[4 * i + 3] = p[0] * th[3] + p[1] * th[4] + p[2] * th[5] + p[3];
+    out[4 * i + 3] = p[0] * th[3] + p[1] * th[4] + p[2] * th[5] + T(p[3]);
   }
 }
 
+// Per-view geometry from a (moved) projection matrix: scaled P (third row of M
+// unit, det M > 0), source as the meet of the rows (Eq. 4, then Eq. 5 with p
+// entering with the opposite sign), up axis m3 x m1, cofactor rows (m2 x m3,
+// m3 x m1, m1 x m2; l = cof(M) n) with the third row for centred detector
+// coordinates, principal point and source-detector distance.  Returns false for
+// a degenerate P.
+template <class T>
+__host__ __device__ bool view_geometry(const T* Pm, int W, int H, T* Pn, T* C, T* up, T* cofc, T* u0, T* v0, T* D) {
+  T m1[3] = {Pm[0], Pm[1], Pm[2]}, m2[3] = {Pm[4], Pm[5], Pm[6]}, m3[3] = {Pm[8], Pm[9], Pm[10]};
+  T c23[3];
+  cross3(m2, m3, c23);
+  const T det = dot3(m1, c23);
+  const T n3 = sqrt(dot3(m3, m3));
+  bool ok = isfinite(value(det)) && isfinite(value(n3)) && value(det) != 0.0 && value(n3) > 0.0;
+  const T sc = ok ? T(copysign(1.0, value(det))) / n3 : T(0.0);
+  for (int k = 0; k < 12; ++k) Pn[k] = Pm[k] * sc;
+  const T* a = Pn;
+  const T* b = Pn + 4;
+  const T* c = Pn + 8;
+  const T p_ = a[2] * b[3] - a[3] * b[2], q_ = a[1] * b[3] - a[3] * b[1], r_ = a[1] * b[2] - a[2] * b[1];
+  const T s_ = a[0] * b[3] - a[3] * b[0], t_ = a[0] * b[2] - a[2] * b[0], u_ = a[0] * b[1] - a[1] * b[0];
+  const T X0 = p_ * c[1] - q_ * c[2] + r_ * c[3];
+  const T X1 = -p_ * c[0] + s_ * c[2] - t_ * c[3];
+  const T X2 = q_ * c[0] - s_ * c[1] + u_ * c[3];
+  const T X3 = -r_ * c[0] + t_ * c[1] - u_ * c[2];
+  ok = ok && value(X3) != 0.0;
+  const T iw = ok ? T(1.0) / X3 : T(0.0);
+  C[0] = X0 * iw;
+  C[1] = X1 * iw;
+  C[2] = X2 * iw;
+  T n1[3] = {Pn[0], Pn[1], Pn[2]}, n2[3] = {Pn[4], Pn[5], Pn[6]}, nn3[3] = {Pn[8], Pn[9], Pn[10]};
+  T upr[3];
+  cross3(nn3, n1, upr);
+  const T nu = sqrt(dot3(upr, upr));
+  ok = ok && value(nu) > 0.0;
+  for (int k = 0; k < 3; ++k) up[k] = ok ? upr[k] / nu : T(0.0);
+  T k0[3], k1[3], k2[3];
+  cross3(n2, nn3, k0);
+  cross3(nn3, n1, k1);
+  cross3(n1, n2, k2);
+  const double cxd = 0.5 * (W - 1), cyd = 0.5 * (H - 1);
+  for (int k = 0; k < 3; ++k) {
+    cofc[k] = k0[k];
+    cofc[3 + k] = k1[k];
+    cofc[6 + k] = cxd * k0[k] + cyd * k1[k] + k2[k];
+  }
+  *u0 = dot3(n1, nn3);
+  *v0 = dot3(n2, nn3);
+  const T dd = dot3(n1, n1) - *u0 * *u0;
+  ok = ok && value(dd) > 0.0;
+  *D = ok ? sqrt(dd) : T(0.0);
+  for (int k = 0; k < 3; ++k) ok = ok && isfinite(value(C[k]));
+  return ok;
+}
+
+// Frame of the pencil of epipolar planes around the baseline C_a -> C_b:
+// u = baseline direction, w = (up_a + up_b) made orthogonal to u (the world axis
+// least aligned with u if that is degenerate), v = w x u; the plane at kappa has
+// normal cos(kappa) w + sin(kappa) v.  Returns false for coincident sources.
+template <class T>
+__host__ __device__ bool pencil_frame(const T* Ca, const T* Cb, const T* upa, const T* upb, T* w, T* v) {
+  T d[3] = {Cb[0] - Ca[0], Cb[1] - Ca[1], Cb[2] - Ca[2]};
+  const T nd = sqrt(dot3(d, d));
+  if (!(value(nd) > 0.0)) return false;
+  T u[3];
+  for (int k = 0; k < 3; ++k) u[k] = d[k] / nd;
+  T rr[3] = {upa[0] + upb[0], upa[1] + upb[1], upa[2] + upb[2]};
+  const T ru = dot3(rr, u);
+  for (int k = 0; k < 3; ++k) w[k] = rr[k] - ru * u[k];
+  T nw = sqrt(dot3(w, w));
+  if (value(nw) < 1e-6) {
+    int ax = 0;
+    double best = fabs(value(u[0]));
+    for (int k = 1; k < 3; ++k)
+      if (fabs(value(u[k])) < best) {
+        best = fabs(value(u[k]));
+        ax = k;
+      }
+    const T ui = u[ax];
+    for (int k = 0; k < 3; ++k) w[k] = T(k == ax ? 1.0 : 0.0) - ui * u[k];
+    nw = sqrt(dot3(w, w));
+  }
+  for (int k = 0; k < 3; ++k) w[k] = w[k] / nw;
+  cross3(w, u, v);
+  return true;
+}
+
 }  // namespace
+
+__host__ __device__ ViewRec setup_view(const double* P, const double* motion, int W, int H) {
+  double Pm[12];
+  if (motion) {
+    moved_projection(P, motion, Pm);
+  } else {
+    for (int k = 0; k < 12; ++k) Pm[k] = P[k];
+  }
+  ViewRec r;
+  r.pad = 0;
+  const bool ok = view_geometry(Pm, W, H, r.P, r.C, r.up, r.cofc, &r.u0, &r.v0, &r.D);
+  r.status = ok ? 0 : 1;
+  return r;
+}
 
 __global__ void view_setup_kernel(int n_views, const double* __restrict__ P, const double* __restrict__ motion,
                                   int W, int H, ViewRec* __restrict__ out, int* __restrict__ status) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_views) return;
-  double Pm[12];
-  if (motion) {
-    moved_projection(P + 12 * i, motion + 6 * i, Pm);
-  } else {
-    for (int k = 0; k < 12; ++k) Pm[k] = P[12 * i + k];
-  }
-  ViewRec r;
-  r.status = 0;
-  r.pad = 0;
-  double m1[3] = {Pm[0], Pm[1], Pm[2]}, m2[3] = {Pm[4], Pm[5], Pm[6]}, m3[3] = {Pm[8], Pm[9], Pm[10]};
-  double c23[3];
-  cross3(m2, m3, c23);
-  const double det = dot3(m1, c23);
-  const double n3 = sqrt(dot3(m3, m3));
-  bool ok = isfinite(det) && isfinite(n3) && det != 0.0 && n3 > 0.0;
-  const double sc = ok ? copysign(1.0, det) / n3 : 0.0;
-  for (int k = 0; k < 12; ++k) r.P[k] = Pm[k] * sc;
-  // source: meet of the first two rows (Pluecker, Eq. 4), then the point where that
-  // line meets the third row, x = L_K P3 (Eq. 5 with p entering with opposite sign)
-  const double* a = r.P;
-  const double* b = r.P + 4;
-  const double* c = r.P + 8;
-  const double p_ = a[2] * b[3] - a[3] * b[2], q_ = a[1] * b[3] - a[3] * b[1], r_ = a[1] * b[2] - a[2] * b[1];
-  const double s_ = a[0] * b[3] - a[3] * b[0], t_ = a[0] * b[2] - a[2] * b[0], u_ = a[0] * b[1] - a[1] * b[0];
-  const double X0 = p_ * c[1] - q_ * c[2] + r_ * c[3];
-  const double X1 = -p_ * c[0] + s_ * c[2] - t_ * c[3];
-  const double X2 = q_ * c[0] - s_ * c[1] + u_ * c[3];
-  const double X3 = -r_ * c[0] + t_ * c[1] - u_ * c[2];
-  ok = ok && X3 != 0.0;
-  const double iw = ok ? 1.0 / X3 : 0.0;
-  r.C[0] = X0 * iw;
-  r.C[1] = X1 * iw;
-  r.C[2] = X2 * iw;
-  double n1[3] = {r.P[0], r.P[1], r.P[2]}, n2[3] = {r.P[4], r.P[5], r.P[6]}, nn3[3] = {r.P[8], r.P[9], r.P[10]};
-  double up[3];
-  cross3(nn3, n1, up);
-  const double nu = sqrt(dot3(up, up));
-  ok = ok && nu > 0.0;
-  for (int k = 0; k < 3; ++k) r.up[k] = ok ? up[k] / nu : 0.0;
-  // cofactor rows: m2 x m3, m3 x m1, m1 x m2 (l = cof(M) n), third row moved to
-  // detector coordinates centred at ((W-1)/2, (H-1)/2)
-  double k0[3], k1[3], k2[3];
-  cross3(n2, nn3, k0);
-  cross3(nn3, n1, k1);
-  cross3(n1, n2, k2);
-  const double cx = 0.5 * (W - 1), cy = 0.5 * (H - 1);
-  for (int k = 0; k < 3; ++k) {
-    r.cofc[k] = k0[k];
-    r.cofc[3 + k] = k1[k];
-    r.cofc[6 + k] = cx * k0[k] + cy * k1[k] + k2[k];
-  }
-  r.u0 = dot3(n1, nn3);
-  r.v0 = dot3(n2, nn3);
-  const double dd = dot3(n1, n1) - r.u0 * r.u0;
-  ok = ok && dd > 0.0;
-  r.D = ok ? sqrt(dd) : 0.0;
-  for (int k = 0; k < 3; ++k) ok = ok && isfinite(r.C[k]);
-  if (!ok) {
-    r.status = 1;
-    atomicOr(status, kStatusDegenerateView);
-  }
+  const ViewRec r = setup_view(P + 12 * i, motion ? motion + 6 * i : nullptr, W, H);
+  if (r.status) atomicOr(status, kStatusDegenerateView);
   out[i] = r;
+}
+
+// Tangents of the per-view geometry with respect to the view's own motion
+// parameters (forward mode, FP64): d C / d theta, d up / d theta, d cofc / d theta.
+__global__ void view_tangent_kernel(int n_views, const double* __restrict__ P, const double* __restrict__ motion,
+                                    int W, int H, ViewTan* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_views) return;
+  using D6 = Dual<6>;
+  D6 th[6];
+  for (int j = 0; j < 6; ++j) {
+    th[j] = D6(motion ? motion[6 * i + j] : 0.0);
+    th[j].d[j] = 1.0;
+  }
+  D6 Pm[12], Pn[12], C[3], up[3], cofc[9], u0, v0, D;
+  moved_projection(P + 12 * i, th, Pm);
+  view_geometry(Pm, W, H, Pn, C, up, cofc, &u0, &v0, &D);
+  ViewTan t;
+  for (int j = 0; j < 6; ++j) {
+    for (int k = 0; k < 3; ++k) {
+      t.dC[k][j] = C[k].d[j];
+      t.dup[k][j] = up[k].d[j];
+    }
+    for (int k = 0; k < 9; ++k) t.dcofc[k][j] = cofc[k].d[j];
+  }
+  out[i] = t;
 }
 
 namespace {
@@ -116,7 +192,7 @@ namespace {
 // the same strict sign, g_c = A^T x_c.  If the g_c lie in a half plane (epipole
 // outside), the valid directions (mod pi) run counter-clockwise from rot90(g_min)
 // over the angle between the extreme g's; otherwise every plane is valid.
-__device__ void view_arc(const double* A, int W, int H, double* clo, double* len) {
+__host__ __device__ double view_arc(const double* A, int W, int H, double* clo) {
   const double xs[4] = {-0.5 * W, 0.5 * W, 0.5 * W, -0.5 * W};
   const double ys[4] = {-0.5 * H, -0.5 * H, 0.5 * H, 0.5 * H};
   double g[4][2];
@@ -141,8 +217,7 @@ __device__ void view_arc(const double* A, int W, int H, double* clo, double* len
   if (degenerate || imin < 0 || imax < 0) {
     clo[0] = 0.0;
     clo[1] = -1.0;
-    *len = kPi;
-    return;
+    return kPi;
   }
   const double cr = g[imin][0] * g[imax][1] - g[imin][1] * g[imax][0];
   const double dt = g[imin][0] * g[imax][0] + g[imin][1] * g[imax][1];
@@ -151,24 +226,18 @@ __device__ void view_arc(const double* A, int W, int H, double* clo, double* len
   const double ng = sqrt(g[imin][0] * g[imin][0] + g[imin][1] * g[imin][1]);
   clo[0] = -g[imin][1] / ng;
   clo[1] = g[imin][0] / ng;
-  *len = phi;
+  return phi;
 }
 
 }  // namespace
 
-__global__ void pair_setup_kernel(int n_views, long long n_pairs, const int32_t* __restrict__ pairs,
-                                  const ViewRec* __restrict__ views, int W, int H, int K,
-                                  PairRec* __restrict__ out, double2* __restrict__ ctile, int n_tiles,
-                                  int* __restrict__ status) {
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n_pairs) return;
-  int a, b;
-  if (pairs) {
-    a = pairs[2 * p];
-    b = pairs[2 * p + 1];
-  } else {
-    pair_from_index(p, n_views, &a, &b);
-  }
+// Per-pair set-up (FP64): frame, kappa -> line maps, valid arcs, the sampled arc,
+// the integer ranges of valid samples and the tile-centre directions (ctile,
+// n_tiles entries).  With previous != NULL the sampling of *previous is kept and
+// only the maps follow the geometry.
+__host__ __device__ PairRec setup_pair(int a, int b, int n_views, const ViewRec* views, int W, int H, int K,
+                                       double2* ctile, int n_tiles, const PairRec* previous) {
+  const bool reuse_sampling = previous != nullptr;
   PairRec r;
   const bool in_range = a >= 0 && b >= 0 && a < n_views && b < n_views;
   if (!in_range) {  // caller's pair list names a view that does not exist
@@ -188,88 +257,207 @@ __global__ void pair_setup_kernel(int n_views, long long n_pairs, const int32_t*
   for (int i = 0; i < 12; ++i) (&r.A[0][0])[i] = 0.0;
   const ViewRec& va = views[a];
   const ViewRec& vb = views[b];
-  double d[3] = {vb.C[0] - va.C[0], vb.C[1] - va.C[1], vb.C[2] - va.C[2]};
-  const double nd = sqrt(dot3(d, d));
-  bool ok = in_range && va.status == 0 && vb.status == 0 && nd > 0.0 && a != b;
-  double u[3] = {0, 0, 0}, w[3] = {0, 0, 0}, v[3] = {0, 0, 0};
+  double w[3] = {0, 0, 0}, v[3] = {0, 0, 0};
+  bool ok = in_range && va.status == 0 && vb.status == 0 && a != b &&
+            pencil_frame(va.C, vb.C, va.up, vb.up, w, v);
   if (ok) {
-    for (int k = 0; k < 3; ++k) u[k] = d[k] / nd;
-    double rr[3] = {va.up[0] + vb.up[0], va.up[1] + vb.up[1], va.up[2] + vb.up[2]};
-    const double ru = dot3(rr, u);
-    for (int k = 0; k < 3; ++k) w[k] = rr[k] - ru * u[k];
-    double nw = sqrt(dot3(w, w));
-    if (nw < 1e-6) {  // up_a + up_b along the baseline: world axis least aligned with u
-      int ax = 0;
-      double best = fabs(u[0]);
-      for (int k = 1; k < 3; ++k)
-        if (fabs(u[k]) < best) { best = fabs(u[k]); ax = k; }
-      const double ui = u[ax];
-      for (int k = 0; k < 3; ++k) w[k] = (k == ax ? 1.0 : 0.0) - ui * u[k];
-      nw = sqrt(dot3(w, w));
-    }
-    for (int k = 0; k < 3; ++k) w[k] /= nw;
-    cross3(w, u, v);
     const ViewRec* vv[2] = {&va, &vb};
     for (int s = 0; s < 2; ++s)
       for (int i = 0; i < 3; ++i) {
         r.A[s][2 * i + 0] = dot3(vv[s]->cofc + 3 * i, w);
         r.A[s][2 * i + 1] = dot3(vv[s]->cofc + 3 * i, v);
       }
-    double clo[2][2], len[2];
-    view_arc(r.A[0], W, H, clo[0], &len[0]);
-    view_arc(r.A[1], W, H, clo[1], &len[1]);
-    const int sv = len[0] <= len[1] ? 0 : 1;  // sample the shorter arc (ties: view a)
-    const int ov = 1 - sv;
-    const double dk = len[sv] / K;
+  }
+  if (ok && reuse_sampling) {
+    // keep the planes sampled by the previous call (kappa arcs and validity
+    // frozen); only the kappa -> line maps follow the new geometry
+    const PairRec old = *previous;
+    r.dk = old.dk;
+    r.c0[0] = old.c0[0];
+    r.c0[1] = old.c0[1];
+    r.rot[0] = old.rot[0];
+    r.rot[1] = old.rot[1];
+    r.r0lo = old.r0lo;
+    r.r0hi = old.r0hi;
+    r.r1lo = old.r1lo;
+    r.r1hi = old.r1hi;
+    r.nk = old.nk;
+    ok = old.status == 0;
+  } else if (ok) {
+    // (scalars and selects only: no dynamically indexed local arrays here)
+    double cla[2], clb[2];
+    const double lena = view_arc(r.A[0], W, H, cla);
+    const double lenb = view_arc(r.A[1], W, H, clb);
+    // sample the shorter arc; ties (equal in exact arithmetic for mirror-symmetric
+    // pairs) go to view a within a relative tolerance, not by rounding
+    const bool samp_a = lena <= lenb + 1e-9 * fmax(lena, lenb);
+    const double len_s = samp_a ? lena : lenb, len_o = samp_a ? lenb : lena;
+    const double csx = samp_a ? cla[0] : clb[0], csy = samp_a ? cla[1] : clb[1];
+    const double cox = samp_a ? clb[0] : cla[0], coy = samp_a ? clb[1] : cla[1];
+    const double dk = len_s / K;
     r.dk = dk;
     double sh, ch;
     sincos(0.5 * dk, &sh, &ch);
-    r.c0[0] = ch * clo[sv][0] - sh * clo[sv][1];
-    r.c0[1] = sh * clo[sv][0] + ch * clo[sv][1];
-    sincos(dk, &r.rot[1], &r.rot[0]);
+    r.c0[0] = ch * csx - sh * csy;
+    r.c0[1] = sh * csx + ch * csy;
+    double srot, crot;
+    sincos(dk, &srot, &crot);
+    r.rot[0] = crot;
+    r.rot[1] = srot;
     // valid samples of the other view: y_k = delta0 + (k + 1/2) dk, valid iff
     // y_k <= len_o or pi <= y_k <= pi + len_o (angles mod pi from its arc start)
-    if (len[ov] >= kPi) {
+    if (len_o >= kPi) {
       r.r0lo = 0;
       r.r0hi = K;
       r.r1lo = r.r1hi = K;
     } else if (dk > 0.0) {
-      double d0 = atan2(clo[ov][0] * clo[sv][1] - clo[ov][1] * clo[sv][0],
-                        clo[ov][0] * clo[sv][0] + clo[ov][1] * clo[sv][1]);
+      double d0 = atan2(cox * csy - coy * csx, cox * csx + coy * csy);
       if (d0 < 0.0) d0 += kPi;
       if (d0 >= kPi) d0 -= kPi;
-      const double e0 = floor((len[ov] - d0) / dk - 0.5);
+      const double e0 = floor((len_o - d0) / dk - 0.5);
       const double s1 = ceil((kPi - d0) / dk - 0.5);
-      const double e1 = floor((kPi + len[ov] - d0) / dk - 0.5);
-      int hi0 = (int)fmin(fmax(e0 + 1.0, 0.0), (double)K);
-      int lo1 = (int)fmin(fmax(s1, (double)hi0), (double)K);
-      int hi1 = (int)fmin(fmax(e1 + 1.0, (double)lo1), (double)K);
+      const double e1 = floor((kPi + len_o - d0) / dk - 0.5);
+      const int hi0 = (int)fmin(fmax(e0 + 1.0, 0.0), (double)K);
+      const int lo1 = (int)fmin(fmax(s1, (double)hi0), (double)K);
+      const int hi1 = (int)fmin(fmax(e1 + 1.0, (double)lo1), (double)K);
       r.r0lo = 0;
       r.r0hi = hi0;
       r.r1lo = lo1;
       r.r1hi = hi1;
     }
     r.nk = (r.r0hi - r.r0lo) + (r.r1hi - r.r1lo);
-    // directions of the tile centres: (32 t + 16) dk from the arc start
+    // directions of the tile centres: tile t holds samples [32t, min(32t + 32, K)),
+    // centred at ((k_begin + k_end) / 2) dk from the arc start; full tiles step by 32 dk
     double s16, c16, s32, c32;
     sincos(16.0 * dk, &s16, &c16);
     sincos(32.0 * dk, &s32, &c32);
-    double cx0 = c16 * clo[sv][0] - s16 * clo[sv][1];
-    double cy0 = s16 * clo[sv][0] + c16 * clo[sv][1];
-    double2* ct = ctile + p * n_tiles;
+    double cx0 = c16 * csx - s16 * csy;
+    double cy0 = s16 * csx + c16 * csy;
+    double2* ct = ctile;
     for (int t = 0; t < n_tiles; ++t) {
-      ct[t] = make_double2(cx0, cy0);
+      if (32 * t + 32 <= K) {
+        ct[t] = make_double2(cx0, cy0);
+      } else {  // last, partial tile
+        double sp, cp;
+        sincos(0.5 * (32.0 * t + K) * dk, &sp, &cp);
+        ct[t] = make_double2(cp * csx - sp * csy, sp * csx + cp * csy);
+      }
       const double nx = c32 * cx0 - s32 * cy0;
       const double ny = s32 * cx0 + c32 * cy0;
       cx0 = nx;
       cy0 = ny;
     }
   }
-  if (!ok) {
-    r.status = 1;
-    atomicOr(status, kStatusDegeneratePair);
+  if (!ok) r.status = 1;
+  return r;
+}
+
+__global__ void pair_setup_kernel(int n_views, long long n_pairs, const int32_t* __restrict__ pairs,
+                                  const ViewRec* __restrict__ views, int W, int H, int K,
+                                  PairRec* __restrict__ out, double2* __restrict__ ctile, int n_tiles,
+                                  int reuse_sampling, int* __restrict__ status) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_pairs) return;
+  int a, b;
+  if (pairs) {
+    a = pairs[2 * p];
+    b = pairs[2 * p + 1];
+  } else {
+    pair_from_index(p, n_views, &a, &b);
   }
+  PairRec prev;
+  if (reuse_sampling) prev = out[p];
+  const PairRec r = setup_pair(a, b, n_views, views, W, H, K, ctile + p * n_tiles, n_tiles,
+                               reuse_sampling ? &prev : nullptr);
+  if (r.status) atomicOr(status, kStatusDegeneratePair);
   out[p] = r;
+}
+
+// Gradient of one pair's e with respect to the 12 motion parameters of its two
+// views: the frame (w, v) and the kappa -> line maps A = cof(M) [w v] are
+// recomputed with forward-mode tangents (FP64), then contracted with
+// G = d e / d A accumulated by the pair kernel (already scaled by de/dd / N).
+__global__ void pair_grad_kernel(long long n_pairs, const PairRec* __restrict__ prs,
+                                 const ViewRec* __restrict__ views, const ViewTan* __restrict__ vtan,
+                                 const double* __restrict__ Gpp, double* __restrict__ gpp) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_pairs) return;
+  const PairRec& pr = prs[p];
+  double* out = gpp + 12 * p;
+  if (pr.status != 0 || pr.nk <= 0) {
+    for (int j = 0; j < 12; ++j) out[j] = 0.0;
+    return;
+  }
+  using D = Dual<12>;
+  const int ab[2] = {pr.a, pr.b};
+  D C[2][3], up[2][3], cof[2][9];
+  for (int s = 0; s < 2; ++s) {
+    const ViewRec& vr = views[ab[s]];
+    const ViewTan& vt = vtan[ab[s]];
+    for (int k = 0; k < 3; ++k) {
+      C[s][k] = D(vr.C[k]);
+      up[s][k] = D(vr.up[k]);
+      for (int j = 0; j < 6; ++j) {
+        C[s][k].d[6 * s + j] = vt.dC[k][j];
+        up[s][k].d[6 * s + j] = vt.dup[k][j];
+      }
+    }
+    for (int k = 0; k < 9; ++k) {
+      cof[s][k] = D(vr.cofc[k]);
+      for (int j = 0; j < 6; ++j) cof[s][k].d[6 * s + j] = vt.dcofc[k][j];
+    }
+  }
+  D w[3], v[3];
+  pencil_frame(C[0], C[1], up[0], up[1], w, v);
+  double g[12];
+  for (int j = 0; j < 12; ++j) g[j] = 0.0;
+  const double* G = Gpp + 12 * p;
+  for (int s = 0; s < 2; ++s)
+    for (int i = 0; i < 3; ++i) {
+      const D aw = dot3(cof[s] + 3 * i, w);
+      const D av = dot3(cof[s] + 3 * i, v);
+      const double g0 = G[6 * s + 2 * i], g1 = G[6 * s + 2 * i + 1];
+      for (int j = 0; j < 12; ++j) g[j] += g0 * aw.d[j] + g1 * av.d[j];
+    }
+  for (int j = 0; j < 12; ++j) out[j] = g[j];
+}
+
+// Per-view sum of the pair gradients in a fixed order (one block per view):
+// deterministic grad[view][6].  With pairs == NULL the pairs of a view are found
+// by the row-major a < b enumeration, otherwise by scanning the pair list.
+__global__ void __launch_bounds__(256) view_grad_reduce_kernel(int n_views, long long n_pairs,
+                                                               const int32_t* __restrict__ pairs,
+                                                               const double* __restrict__ gpp,
+                                                               double* __restrict__ grad) {
+  __shared__ double sh[6][256];
+  const int lam = blockIdx.x;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  if (pairs) {
+    for (long long p = threadIdx.x; p < n_pairs; p += blockDim.x) {
+      const int a = pairs[2 * p], b = pairs[2 * p + 1];
+      if (a == lam)
+        for (int j = 0; j < 6; ++j) acc[j] += gpp[12 * p + j];
+      if (b == lam)
+        for (int j = 0; j < 6; ++j) acc[j] += gpp[12 * p + 6 + j];
+    }
+  } else {
+    const long long n = n_views;
+    for (int o = threadIdx.x; o < n_views; o += blockDim.x) {
+      if (o == lam) continue;
+      const long long a = o < lam ? o : lam, b = o < lam ? lam : o;
+      const long long p = a * (2 * n - a - 1) / 2 + (b - a - 1);
+      const int off = o < lam ? 6 : 0;  // this view is b of the pair when o < lam
+      for (int j = 0; j < 6; ++j) acc[j] += gpp[12 * p + off + j];
+    }
+  }
+  for (int j = 0; j < 6; ++j) sh[j][threadIdx.x] = acc[j];
+  __syncthreads();
+  for (int wdt = blockDim.x / 2; wdt > 0; wdt >>= 1) {
+    if (threadIdx.x < wdt)
+      for (int j = 0; j < 6; ++j) sh[j][threadIdx.x] += sh[j][threadIdx.x + wdt];
+    __syncthreads();
+  }
+  if (threadIdx.x < 6) grad[6 * lam + threadIdx.x] = sh[threadIdx.x][0];
 }
 
 // Row directions (cos, sin)(m pi / n_alpha) in FP64 for the anchor look-ups.
@@ -282,3 +470,32 @@ __global__ void alpha_dir_kernel(int n_alpha, double2* __restrict__ dir) {
 }
 
 }  // namespace ecc
+
+// Internal host entry point (tests only, not part of the public ABI): runs the
+// per-view and per-pair set-up above on the CPU for views (a, b) of a scan so
+// that the set-up logic can be checked without a GPU.
+//   P host FP64 [n_views][12], motion host FP64 [n_views][6] or NULL
+//   info_out [8]: sampled-arc start direction of sample 0 (c0x, c0y), dk, nk,
+//                 status, r0hi, r1lo, r1hi
+//   A_out [12]: the kappa -> line maps of views a and b
+extern "C" int ecc_internal_setup_pair_host(int n_views, const double* P, const double* motion, int W, int H, int K,
+                                            int a, int b, double* info_out, double* A_out) {
+  if (n_views < 1 || a < 0 || b < 0 || a >= n_views || b >= n_views || K < 1) return -1;
+  ecc::ViewRec views[2];
+  views[0] = ecc::setup_view(P + 12 * a, motion ? motion + 6 * a : nullptr, W, H);
+  views[1] = ecc::setup_view(P + 12 * b, motion ? motion + 6 * b : nullptr, W, H);
+  const int n_tiles = (K + 31) / 32;
+  double2* ct = new double2[n_tiles];
+  const ecc::PairRec r = ecc::setup_pair(0, 1, 2, views, W, H, K, ct, n_tiles, nullptr);
+  delete[] ct;
+  info_out[0] = r.c0[0];
+  info_out[1] = r.c0[1];
+  info_out[2] = r.dk;
+  info_out[3] = r.nk;
+  info_out[4] = r.status;
+  info_out[5] = r.r0hi;
+  info_out[6] = r.r1lo;
+  info_out[7] = r.r1hi;
+  for (int i = 0; i < 12; ++i) A_out[i] = (&r.A[0][0])[i];
+  return 0;
+}

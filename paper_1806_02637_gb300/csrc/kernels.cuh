@@ -9,7 +9,13 @@ namespace ecc {
 __global__ void view_setup_kernel(int n_views, const double* P, const double* motion, int W, int H, ViewRec* out,
                                   int* status);
 __global__ void pair_setup_kernel(int n_views, long long n_pairs, const int32_t* pairs, const ViewRec* views, int W,
-                                  int H, int K, PairRec* out, double2* ctile, int n_tiles, int* status);
+                                  int H, int K, PairRec* out, double2* ctile, int n_tiles, int reuse_sampling,
+                                  int* status);
+__global__ void view_tangent_kernel(int n_views, const double* P, const double* motion, int W, int H, ViewTan* out);
+__global__ void pair_grad_kernel(long long n_pairs, const PairRec* prs, const ViewRec* views, const ViewTan* vtan,
+                                 const double* Gpp, double* gpp);
+__global__ void view_grad_reduce_kernel(int n_views, long long n_pairs, const int32_t* pairs, const double* gpp,
+                                        double* grad);
 __global__ void alpha_dir_kernel(int n_alpha, double2* dir);
 
 // Per (view, alpha-row) line parameters of the Joseph line sums (32.32 fixed point).
@@ -43,13 +49,16 @@ struct LaunchHooks {
 
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_radon(const ViewRec* views, int n_views, const float* images, int W, int H, int n_alpha, int n_s,
-                         int dtype, void* sino_out, float* scales_out, RadonRow* table, float* wimg,
+                         int dtype, void* sino_out, float* scales_out, RadonRow* table, float* wimg, float* stage,
                          int batch_views, const LaunchHooks& hooks, cudaStream_t stream);
+size_t radon_f16_stage_bytes(int n_alpha, int n_s, int batch_views);
+int radon_pad(int W, int H, int n_s);
+size_t radon_plane_floats(int W, int H, int n_s);
 
 cudaError_t launch_ecc_pairs(long long n_pairs, const PairRec* prs, const double2* ctile, int n_tiles,
                              const double2* alpha_dir, const void* sino, const float* scales, int dtype,
                              int n_alpha, int n_s, int K, double inv_ds, double cauchy_c, double* per_pair, int32_t* nk_out,
-                             double* block_partial, int* n_blocks_out, const LaunchHooks& hooks,
+                             double* block_partial, double* Gpp, int* n_blocks_out, const LaunchHooks& hooks,
                              cudaStream_t stream);
 
 cudaError_t launch_reduce(const double* partial, int n, double* total, const LaunchHooks& hooks,

@@ -14,7 +14,8 @@
 //                        columns, linear interpolation along the other axis).  The
 //                        half-step difference in s is formed tap by tap between
 //                        neighbouring lanes (warp shuffle) so that it never cancels
-//                        two large FP32 sums; the (D^2 + s^2)/D^2 weight is applied
+//                        two large FP32 sums (block sums of the differences are
+//                        Kahan-compensated); the (D^2 + s^2)/D^2 weight is applied
 //                        at the end.  Lanes read consecutive floats of one image
 //                        row: coalesced, L1/L2 resident.
 #include <cuda_bf16.h>
@@ -72,16 +73,16 @@ __global__ void radon_table_kernel(const ViewRec* __restrict__ views, int n_view
   }
 }
 
-// Weighted projection, row-major [H][W+4] and transposed [W][H+4] (data from
-// column / row 2).  Block (32, 8) over a 32x32 tile; the transpose goes through
-// shared memory so both writes are coalesced.
+// Weighted projection, row-major [H][W + 2 pad] and transposed [W][H + 2 pad]
+// (data from column / row pad, zeros elsewhere).  Block (32, 8) over a 32x32 tile;
+// the transpose goes through shared memory so both writes are coalesced.
 __global__ void weight_kernel(const float* __restrict__ images, const RadonView* __restrict__ rv, int W, int H,
-                              float* __restrict__ wimg, size_t plane) {
+                              int pad, float* __restrict__ wimg, size_t plane) {
   __shared__ float tile[32][33];
   const int v = blockIdx.z;
   const float* g = images + (size_t)v * W * H;
   float* R = wimg + (size_t)v * plane;
-  float* T = R + (size_t)H * (W + 4);
+  float* T = R + (size_t)H * (W + 2 * pad);
   const RadonView r = rv[v];
   const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
   for (int j = 0; j < 4; ++j) {
@@ -90,14 +91,14 @@ __global__ void weight_kernel(const float* __restrict__ images, const RadonView*
     if (x < W && y < H) {
       const float du = (float)x - r.u0, dv = (float)y - r.v0;
       w = g[(size_t)y * W + x] * (r.D / sqrtf(r.D * r.D + du * du + dv * dv));
-      R[(size_t)y * (W + 4) + x + 2] = w;
+      R[(size_t)y * (W + 2 * pad) + x + pad] = w;
     }
     tile[threadIdx.y + 8 * j][threadIdx.x] = w;
   }
   __syncthreads();
   for (int j = 0; j < 4; ++j) {
     const int xo = bx + threadIdx.y + 8 * j, yo = by + threadIdx.x;
-    if (xo < W && yo < H) T[(size_t)xo * (H + 4) + yo + 2] = tile[threadIdx.x][threadIdx.y + 8 * j];
+    if (xo < W && yo < H) T[(size_t)xo * (H + 2 * pad) + yo + pad] = tile[threadIdx.x][threadIdx.y + 8 * j];
   }
 }
 
@@ -110,11 +111,15 @@ __device__ __forceinline__ void store_out<__half>(__half* p, float v) { *p = __f
 template <>
 __device__ __forceinline__ void store_out<__nv_bfloat16>(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 
-template <typename OutT>
+// CLAMP = false: the zero margin (pad) is wider than the span of a warp's 32 lines
+// plus the step-range margins, so every tap read stays inside the padded row
+// without clamping.  CLAMP = true (coarse s grids): pad = 2 and the coordinate is
+// clamped onto the zero columns.
+template <typename OutT, bool CLAMP>
 __global__ void __launch_bounds__(256) joseph_kernel(const RadonRow* __restrict__ table,
                                                      const RadonView* __restrict__ rv,
                                                      const float* __restrict__ wimg, size_t plane, int W, int H,
-                                                     int n_alpha, int n_s, float ds, int warps_per_block,
+                                                     int pad, int n_alpha, int n_s, float ds, int warps_per_block,
                                                      OutT* __restrict__ out) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -125,8 +130,8 @@ __global__ void __launch_bounds__(256) joseph_kernel(const RadonRow* __restrict_
   const int k = k0 + lane;
   const RadonRow row = table[(size_t)v * n_alpha + m];
   const bool rows = row.rows_mode != 0;
-  const float* img = wimg + (size_t)v * plane + (rows ? 0 : (size_t)H * (W + 4));
-  const int pitch = rows ? W + 4 : H + 4;
+  const float* img = wimg + (size_t)v * plane + (rows ? 0 : (size_t)H * (W + 2 * pad));
+  const int pitch = rows ? W + 2 * pad : H + 2 * pad;
   const int n_steps = rows ? H : W;
   const int limit = rows ? W : H;
   // steps where some lane of the warp is inside the interpolation support
@@ -152,40 +157,50 @@ __global__ void __launch_bounds__(256) joseph_kernel(const RadonRow* __restrict_
     if (s_hi < s_lo) s_hi = s_lo;
   }
   long long X = row.B0 + (long long)k * row.STEP + (long long)s_lo * row.DY;
-  const float* base = img + (size_t)s_lo * pitch + 2;
-  float part = 0.0f, acc = 0.0f;
+  const float* base = img + (size_t)s_lo * pitch + pad;
+  // Each step: tap t_j of this lane's line, t_{j+1} of the neighbour's (next sigma)
+  // by shuffle, and their difference, which is small and (for neighbouring taps of
+  // a smooth image) exact in FP32.  Differences are summed in 8-step blocks; the
+  // block sums are added with Kahan compensation.
+  float q = 0.0f, acc = 0.0f, comp = 0.0f;
   int s = s_lo;
-  for (; s + 4 <= s_hi; s += 4) {
+  for (; s + 8 <= s_hi; s += 8) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 8; ++u) {
       int xi = (int)(X >> 32);
       const unsigned lo = (unsigned)(X & 0xffffffffLL);
       const float f = __uint_as_float(0x3f800000u | (lo >> 9)) - 1.0f;
-      xi = min(max(xi, -2), limit);
+      if (CLAMP) xi = min(max(xi, -2), limit);
       const float* rp = base + xi;
       const float v0 = __ldg(rp), v1 = __ldg(rp + 1);
-      part += fmaf(f, v1 - v0, v0);
+      const float t = fmaf(f, v1 - v0, v0);
+      const float nb = __shfl_down_sync(0xffffffffu, t, 1);
+      q += nb - t;
       X += row.DY;
       base += pitch;
     }
-    const float nb = __shfl_down_sync(0xffffffffu, part, 1);
-    acc += nb - part;
-    part = 0.0f;
+    const float y = q - comp;
+    const float tt = acc + y;
+    comp = (tt - acc) - y;
+    acc = tt;
+    q = 0.0f;
   }
   for (; s < s_hi; ++s) {
     int xi = (int)(X >> 32);
     const unsigned lo = (unsigned)(X & 0xffffffffLL);
     const float f = __uint_as_float(0x3f800000u | (lo >> 9)) - 1.0f;
-    xi = min(max(xi, -2), limit);
+    if (CLAMP) xi = min(max(xi, -2), limit);
     const float* rp = base + xi;
     const float v0 = __ldg(rp), v1 = __ldg(rp + 1);
-    part += fmaf(f, v1 - v0, v0);
+    const float t = fmaf(f, v1 - v0, v0);
+    const float nb = __shfl_down_sync(0xffffffffu, t, 1);
+    q += nb - t;
     X += row.DY;
     base += pitch;
   }
   {
-    const float nb = __shfl_down_sync(0xffffffffu, part, 1);
-    acc += nb - part;
+    const float y = q - comp;
+    acc = acc + y;
   }
   if (lane < 31 && k < n_s) {
     const RadonView r = rv[v];
@@ -196,12 +211,53 @@ __global__ void __launch_bounds__(256) joseph_kernel(const RadonRow* __restrict_
   }
 }
 
+// FP16 storage: per-view scale = max|S| / 2^14 (1 if the view is all zero), so
+// every stored value is in FP16's normal range; stored = S / scale.
+__global__ void __launch_bounds__(256) absmax_scale_kernel(const float* __restrict__ s32, size_t per_view,
+                                                          float* __restrict__ scales) {
+  __shared__ float sh[256];
+  const float* p = s32 + (size_t)blockIdx.x * per_view;
+  float m = 0.0f;
+  for (size_t i = threadIdx.x; i < per_view; i += blockDim.x) m = fmaxf(m, fabsf(p[i]));
+  sh[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] = fmaxf(sh[threadIdx.x], sh[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) scales[blockIdx.x] = sh[0] > 0.0f ? sh[0] / 16384.0f : 1.0f;
+}
+
+__global__ void quantize_f16_kernel(const float* __restrict__ s32, size_t per_view, size_t n,
+                                    const float* __restrict__ scales, __half* __restrict__ out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[i] = __float2half_rn(s32[i] / scales[i / per_view]);
+}
+
 }  // namespace
+
+int radon_pad(int W, int H, int n_s) {
+  // span of 32 neighbouring lines along the interpolation axis (|cos| or |sin| >=
+  // 1/sqrt 2 in their mode) plus the margins of the per-warp step range
+  const double ds = sqrt((double)W * W + (double)H * H) / (n_s - 1);
+  const int need = (int)ceil(31.0 * ds * 1.41421356237309515 + 8.0);
+  const int pad = (need + 3) / 4 * 4;
+  return pad <= 160 ? pad : 2;  // 2: clamped variant
+}
+
+size_t radon_plane_floats(int W, int H, int n_s) {
+  const int pad = radon_pad(W, H, n_s);
+  return (size_t)H * (W + 2 * pad) + (size_t)W * (H + 2 * pad);
+}
+
+size_t radon_f16_stage_bytes(int n_alpha, int n_s, int batch_views) {
+  return sizeof(float) * (size_t)n_alpha * n_s * batch_views;
+}
 
 cudaError_t launch_radon(const ViewRec* views, int n_views, const float* images, int W, int H, int n_alpha, int n_s,
                          int dtype, void* sino_out, float* scales_out, RadonRow* table, float* wimg,
-                         int batch_views, const LaunchHooks& hooks, cudaStream_t stream) {
-  (void)scales_out;
+                         float* stage, int batch_views, const LaunchHooks& hooks, cudaStream_t stream) {
   // table and per-view weights (RadonView array sits right after the table)
   RadonView* rv = reinterpret_cast<RadonView*>(table + (size_t)n_views * n_alpha);
   {
@@ -213,7 +269,9 @@ cudaError_t launch_radon(const ViewRec* views, int n_views, const float* images,
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  const size_t plane = (size_t)H * (W + 4) + (size_t)W * (H + 4);
+  const int pad = radon_pad(W, H, n_s);
+  const bool clamp = pad == 2;
+  const size_t plane = radon_plane_floats(W, H, n_s);
   const float ds = (float)(sqrt((double)W * W + (double)H * H) / (n_s - 1));
   const int n_chunks = (n_s + 30) / 31;
   const int blocks_x = (n_chunks + 7) / 8;
@@ -224,31 +282,50 @@ cudaError_t launch_radon(const ViewRec* views, int n_views, const float* images,
     if (e != cudaSuccess) return e;
     hooks.on_begin("weight_kernel", stream);
     weight_kernel<<<dim3((W + 31) / 32, (H + 31) / 32, nb), dim3(32, 8), 0, stream>>>(
-        images + (size_t)v0 * W * H, rv + v0, W, H, wimg, plane);
+        images + (size_t)v0 * W * H, rv + v0, W, H, pad, wimg, plane);
     hooks.on_end("weight_kernel", stream);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const dim3 grid(blocks_x, n_alpha, nb), block(32 * wpb);
     const RadonRow* tb = table + (size_t)v0 * n_alpha;
     hooks.on_begin("joseph_kernel", stream);
+#define JOSEPH(OT, OUTPTR)                                                                                    \
+  do {                                                                                                      \
+    if (clamp)                                                                                              \
+      joseph_kernel<OT, true><<<grid, block, 0, stream>>>(tb, rv + v0, wimg, plane, W, H, pad, n_alpha, n_s, \
+                                                          ds, wpb, OUTPTR);                                   \
+    else                                                                                                    \
+      joseph_kernel<OT, false><<<grid, block, 0, stream>>>(tb, rv + v0, wimg, plane, W, H, pad, n_alpha, n_s, \
+                                                           ds, wpb, OUTPTR);                                  \
+  } while (0)
     switch (dtype) {
       case 0:
-        joseph_kernel<float><<<grid, block, 0, stream>>>(tb, rv + v0, wimg, plane, W, H, n_alpha, n_s, ds, wpb,
-                                                         (float*)sino_out + (size_t)v0 * n_alpha * n_s);
+        JOSEPH(float, (float*)sino_out + (size_t)v0 * n_alpha * n_s);
         break;
-      case 1:
-        joseph_kernel<__half><<<grid, block, 0, stream>>>(tb, rv + v0, wimg, plane, W, H, n_alpha, n_s, ds, wpb,
-                                                          (__half*)sino_out + (size_t)v0 * n_alpha * n_s);
+      case 1:  // FP32 into the staging buffer; scaled and rounded to FP16 below
+        JOSEPH(float, stage);
         break;
       default:
-        joseph_kernel<__nv_bfloat16><<<grid, block, 0, stream>>>(
-            tb, rv + v0, wimg, plane, W, H, n_alpha, n_s, ds, wpb,
-            (__nv_bfloat16*)sino_out + (size_t)v0 * n_alpha * n_s);
+        JOSEPH(__nv_bfloat16, (__nv_bfloat16*)sino_out + (size_t)v0 * n_alpha * n_s);
         break;
     }
+#undef JOSEPH
     hooks.on_end("joseph_kernel", stream);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (dtype == 1) {
+      const size_t per_view = (size_t)n_alpha * n_s;
+      hooks.on_begin("absmax_scale_kernel", stream);
+      absmax_scale_kernel<<<nb, 256, 0, stream>>>(stage, per_view, scales_out + v0);
+      hooks.on_end("absmax_scale_kernel", stream);
+      const size_t n = per_view * nb;
+      hooks.on_begin("quantize_f16_kernel", stream);
+      quantize_f16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(
+          stage, per_view, n, scales_out + v0, (__half*)sino_out + (size_t)v0 * per_view);
+      hooks.on_end("quantize_f16_kernel", stream);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
   }
   return cudaSuccess;
 }

@@ -1,0 +1,142 @@
+"""Gradient of the total (Eq. 17) with respect to per-view rigid motion, from the
+library's adjoint kernel (through the C ABI), against the oracle's complex-step
+gradient, central finite differences of the library's frozen forward, the rigid
+null space, and the torch.autograd.Function wrapper."""
+import functools
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import oracle as orc
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+# gradient parity: relative L2 error of the whole gradient; FP32 per-sample terms
+# and the rare bilinear-cell choices at grid lines (the slopes are cell-wise
+# constant) bound it
+TOL_GRAD = 1e-4
+
+
+@functools.lru_cache(maxsize=None)
+def _ctx():
+    import paper_1806_02637_gb300 as ecc
+    return ecc.Context(0)
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+VIEWS = tuple(range(0, 248, 13))   # 20 views of the 248-view motion workload
+
+
+@functools.lru_cache(maxsize=None)
+def _case():
+    cfg = synth.CONFIGS["c3"]
+    sc = H.scan("c3", VIEWS)
+    S = H.oracle_sino("c3", VIEWS)
+    return cfg, sc, S
+
+
+def _gpu_grad(P, S32, W, Hh, K, c, motion, pairs=None):
+    import paper_1806_02637_gb300 as ecc
+    r = ecc.ecc_evaluate_grad(_ctx(), _cuda(P), _cuda(S32), W, Hh, K, cauchy_c=c, motion=_cuda(motion),
+                              pairs=None if pairs is None else _cuda(np.asarray(pairs, np.int32)))
+    torch.cuda.synchronize()
+    return float(r["total"].cpu()[0]), r["grad"].cpu().numpy(), r["per_pair"].cpu().numpy()
+
+
+@pytest.mark.parametrize("c", [0.0, "median"])
+def test_grad_matches_oracle(c):
+    cfg, sc, S = _case()
+    S32 = S.astype(np.float32)
+    th = sc["motion"]
+    if c == "median":
+        c = float(np.median(orc.ecc(sc["P"], S32.astype(np.float64), cfg.W, cfg.H, cfg.K, motion=th)["d"]))
+    total, g, _ = _gpu_grad(sc["P"], S32, cfg.W, cfg.H, cfg.K, c, th)
+    ref = orc.ecc_grad(sc["P"], S32.astype(np.float64), cfg.W, cfg.H, cfg.K, cauchy_c=c, motion=th)
+    err = np.linalg.norm(g - ref["grad"]) / np.linalg.norm(ref["grad"])
+    assert err <= TOL_GRAD, err
+    assert np.abs(g - ref["grad"]).max() <= 10 * TOL_GRAD * np.abs(ref["grad"]).max()
+    assert abs(total - ref["total"]) <= H.TOL_F32 * ref["total"]
+
+
+def test_grad_explicit_pairs_and_zero_motion():
+    cfg, sc, S = _case()
+    S32 = S.astype(np.float32)
+    n = len(VIEWS)
+    rng = np.random.default_rng(9)
+    pairs = np.array([(a, b) for a in range(n) for b in range(n) if a != b])[rng.choice(n * (n - 1), 120, False)]
+    th = np.zeros((n, 6))
+    total, g, _ = _gpu_grad(sc["P"], S32, cfg.W, cfg.H, cfg.K, 0.0, th, pairs)
+    ref = orc.ecc_grad(sc["P"], S32.astype(np.float64), cfg.W, cfg.H, cfg.K, motion=th, pairs=pairs)
+    assert np.linalg.norm(g - ref["grad"]) <= TOL_GRAD * np.linalg.norm(ref["grad"])
+
+
+def test_grad_vs_central_differences_of_frozen_forward():
+    """Central differences of the library's own forward with the sampled planes
+    frozen (ecc_evaluate_frozen), h = 1e-4 on 32 random parameters."""
+    import paper_1806_02637_gb300 as ecc
+    cfg, sc, S = _case()
+    S32 = _cuda(S.astype(np.float32))
+    th = sc["motion"]
+    P = _cuda(sc["P"])
+    r = ecc.ecc_evaluate_grad(_ctx(), P, S32, cfg.W, cfg.H, cfg.K, motion=_cuda(th))
+    g = r["grad"].cpu().numpy()
+    picks = np.random.default_rng(32).choice(th.size, 32, replace=False)
+    h = 1e-4
+    fd = []
+    for q in picks:
+        vals = []
+        for sgn in (1, -1):
+            t = th.copy()
+            t.flat[q] += sgn * h
+            rr = ecc.ecc_evaluate_frozen(_ctx(), P, S32, cfg.W, cfg.H, cfg.K, motion=_cuda(t))
+            torch.cuda.synchronize()
+            vals.append(float(rr["total"].cpu()[0]))
+        fd.append((vals[0] - vals[1]) / (2 * h))
+    fd = np.array(fd)
+    an = g.flat[picks]
+    # h = 1e-4 rad moves lines by ~0.1 px across the kinks of the bilinear look-up
+    assert np.linalg.norm(fd - an) <= 0.35 * np.linalg.norm(an)
+    assert np.sign(fd @ an) > 0
+
+
+def test_frozen_forward_equals_forward_at_the_same_point():
+    import paper_1806_02637_gb300 as ecc
+    cfg, sc, S = _case()
+    S32 = _cuda(S.astype(np.float32))
+    P, m = _cuda(sc["P"]), _cuda(sc["motion"])
+    a = ecc.ecc_evaluate(_ctx(), P, S32, cfg.W, cfg.H, cfg.K, motion=m)
+    b = ecc.ecc_evaluate_frozen(_ctx(), P, S32, cfg.W, cfg.H, cfg.K, motion=m)
+    torch.cuda.synchronize()
+    assert torch.equal(a["per_pair"], b["per_pair"]) and torch.equal(a["nkappa"], b["nkappa"])
+    with pytest.raises(ecc.EccError):   # a different pair set has no frozen sampling
+        ecc.ecc_evaluate_frozen(_ctx(), P, S32, cfg.W, cfg.H, cfg.K - 1, motion=m)
+
+
+def test_grad_rigid_null_space():
+    cfg, sc, S = _case()
+    rng = np.random.default_rng(4)
+    Sn = (S + rng.normal(0, 0.05 * np.abs(S).max(), S.shape)).astype(np.float32)
+    n = len(VIEWS)
+    _, g, _ = _gpu_grad(sc["P"], Sn, cfg.W, cfg.H, cfg.K, 0.0, np.zeros((n, 6)))
+    col = g.sum(axis=0)
+    assert np.all(np.abs(col) <= 1e-4 * np.abs(g).max(axis=0) * np.sqrt(n)), col
+
+
+def test_autograd_function():
+    import paper_1806_02637_gb300 as ecc
+    cfg, sc, S = _case()
+    S32 = _cuda(S.astype(np.float32))
+    P = _cuda(sc["P"])
+    m = _cuda(sc["motion"]).requires_grad_(True)
+    tot = ecc.consistency(_ctx(), m, P, S32, cfg.W, cfg.H, cfg.K)
+    (gm,) = torch.autograd.grad(2.0 * tot, m)
+    r = ecc.ecc_evaluate_grad(_ctx(), P, S32, cfg.W, cfg.H, cfg.K, motion=m.detach())
+    torch.cuda.synchronize()
+    assert torch.allclose(gm, 2.0 * r["grad"], rtol=0, atol=0)
+    assert float(tot) == float(r["total"][0])
