@@ -136,9 +136,12 @@ __device__ Anchor make_anchor(const double* __restrict__ A, double2 c, const dou
   r.fs0 = (float)(is - nf) - sigf * 2.0f * sh * sh * inv_ds_f;
   r.s0 = sigf * cosf(th);
   // exact first-order advance of the s index per sample: (ds/dkappa) dk / ds_bin in
-  // FP64, ds/dkappa = (1/h) (-l2' + l2 (l . l') / h^2), 1/h = cos(th) / dt
-  const double thd = (double)th;
-  const double ihd = rr * (1.0 - 0.5 * thd * thd * (1.0 - thd * thd * (1.0 / 12.0)));
+  // FP64, ds/dkappa = (1/h) (-l2' + l2 (l . l') / h^2); 1/h from an FP32 reciprocal
+  // square-root seed and one FP64 Newton step (relative error ~1e-13; th may reach a
+  // whole alpha row spacing, so no series in th is used here)
+  const double h2 = fma(l0, l0, l1 * l1);
+  double ihd = (double)rsqrtf((float)h2);
+  ihd = ihd * fma(-0.5 * h2, ihd * ihd, 1.5);
   const double t1 = l0 * p0 + l1 * p1;
   const double g = ihd * (-p2 + l2 * t1 * ihd * ihd) * dk * inv_ds;
   const float gh = __int_as_float(__float_as_int((float)g) & (int)0xffffffc0);
