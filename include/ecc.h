@@ -199,6 +199,35 @@ int ecc_scan_consistency_host(ecc_ctx* ctx, int n_views, const double* P_host, c
                               int H, int n_alpha, int n_s, int n_kappa, double cauchy_c, double* total_host,
                               void* stream);
 
+/*
+ * Allocation-free ecc_evaluate.  The paper has no counterpart: this is a service of
+ * the library, not a step of the method.  It computes exactly what ecc_evaluate
+ * computes, with the same arguments minus the context, for callers that must not
+ * allocate device memory while running (an application that gives all free device
+ * memory to its own pool at start-up, or a fixed-budget pipeline that cannot take
+ * an allocation's implicit device synchronisation).  Its scratch lives in one
+ * 4 MiB statically sized device array inside the library; it calls no allocator.
+ *
+ *   Device: the current CUDA device; all device pointers must be on it.  The first
+ *   call on each device resolves the scratch array's address (cudaGetSymbolAddress
+ *   with that device current) and caches it: make that first call outside any
+ *   stream capture.
+ *   Limits of the static scratch (ECC_EINVAL with a message naming the limit
+ *   otherwise): n_views <= 512, n_alpha <= 4096, n_pairs <= 8192 and
+ *   n_pairs * ceil(n_kappa / 32) <= 131072; the other limits are ecc_evaluate's.
+ *   Concurrency: every call on a device shares the one scratch array, so calls
+ *   that overlap on the GPU race and give wrong results; serialise them (one
+ *   stream, or wait for the previous call's stream).
+ *   Device status bits are not reported (degenerate pairs still give
+ *   N_kappa = 0 and d = e = 0).
+ *   err: host buffer of err_len bytes receiving a NUL-terminated message on error
+ *   (empty string on success), or NULL.
+ */
+int ecc_evaluate_noalloc(int n_views, const double* P, const double* motion, const void* sino, const float* scales,
+                         int W, int H, int n_alpha, int n_s, int dtype, int n_kappa, double cauchy_c,
+                         const int32_t* pairs, int n_pairs, double* total, double* per_pair, int32_t* nkappa,
+                         void* stream, char* err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

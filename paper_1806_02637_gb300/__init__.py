@@ -22,7 +22,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["EccError", "Context", "library_path", "load", "ecc_precompute_radon_derivative", "ecc_evaluate",
-           "ecc_evaluate_grad", "ecc_evaluate_frozen", "consistency",
+           "ecc_evaluate_grad", "ecc_evaluate_frozen", "ecc_evaluate_noalloc", "consistency",
            "ecc_scan_consistency_host", "ecc_status", "ecc_kernel_launches", "ecc_profile_enable",
            "ecc_profile_read", "ECC_F32", "ECC_F16", "ECC_BF16"]
 
@@ -70,6 +70,9 @@ def load(build_if_missing: bool = True):
         lib.ecc_scan_consistency_host.restype = i
         lib.ecc_evaluate_grad.argtypes = [vp, i, vp, vp, vp, vp, i, i, i, i, i, i, d, vp, i, vp, vp, vp, vp, vp]
         lib.ecc_evaluate_grad.restype = i
+        lib.ecc_evaluate_noalloc.argtypes = [i, vp, vp, vp, vp, i, i, i, i, i, i, d, vp, i, vp, vp, vp, vp,
+                                             ctypes.c_char_p, sz]
+        lib.ecc_evaluate_noalloc.restype = i
         lib.ecc_evaluate_frozen.argtypes = [vp, i, vp, vp, vp, vp, i, i, i, i, i, i, d, vp, i, vp, vp, vp, vp]
         lib.ecc_evaluate_frozen.restype = i
         lib.ecc_kernel_launches.argtypes = [vp]
@@ -237,6 +240,46 @@ def ecc_evaluate_frozen(ctx: Context, P, sino, W: int, H: int, n_kappa: int, cau
                                     sino.shape[1], sino.shape[2], code, int(n_kappa), float(cauchy_c), _ptr(pairs),
                                     int(n_pairs), _ptr(total), _ptr(per_pair), _ptr(nkappa), _stream(stream))
     _check(ctx, rc, "ecc_evaluate_frozen")
+    return {"total": total, "per_pair": per_pair, "nkappa": nkappa}
+
+
+def ecc_evaluate_noalloc(P, sino, W: int, H: int, n_kappa: int, total, cauchy_c: float = 0.0, motion=None,
+                         pairs=None, scales=None, per_pair=None, nkappa=None, stream=None) -> dict:
+    """ecc_evaluate without a context and without device allocation: the caller
+    passes every output (total [1] float64; per_pair [n_pairs, 2] float64 and
+    nkappa [n_pairs] int32 optional) and the library uses its static scratch.
+    Runs on the device of sino.  Calls on one device must not overlap on the GPU."""
+    torch = _torch()
+    code = _dtype_code(sino.dtype)
+    N = sino.shape[0]
+    _dev(sino, sino.dtype, "sino")
+    _dev(P, torch.float64, "P", (N, 3, 4))
+    if motion is not None:
+        _dev(motion, torch.float64, "motion", (N, 6))
+    if pairs is not None:
+        _dev(pairs, torch.int32, "pairs")
+        if pairs.dim() != 2 or pairs.shape[1] != 2:
+            raise EccError("pairs must be [n_pairs, 2]")
+        n_pairs = pairs.shape[0]
+    else:
+        n_pairs = N * (N - 1) // 2
+    if code == ECC_F16:
+        _dev(scales, torch.float32, "scales", (N,))
+    else:
+        scales = None
+    _dev(total, torch.float64, "total", (1,))
+    if per_pair is not None:
+        _dev(per_pair, torch.float64, "per_pair", (n_pairs, 2))
+    if nkappa is not None:
+        _dev(nkappa, torch.int32, "nkappa", (n_pairs,))
+    err = ctypes.create_string_buffer(512)
+    with torch.cuda.device(sino.device):
+        rc = load().ecc_evaluate_noalloc(N, _ptr(P), _ptr(motion), _ptr(sino), _ptr(scales), int(W), int(H),
+                                         sino.shape[1], sino.shape[2], code, int(n_kappa), float(cauchy_c),
+                                         _ptr(pairs), int(n_pairs), _ptr(total), _ptr(per_pair), _ptr(nkappa),
+                                         _stream(stream), err, len(err))
+    if rc != ECC_OK:
+        raise EccError(f"ecc_evaluate_noalloc failed ({rc}): {err.value.decode()}")
     return {"total": total, "per_pair": per_pair, "nkappa": nkappa}
 
 
