@@ -160,10 +160,10 @@ int run_precompute(ecc_ctx* c, int n_views, const double* P, const float* images
   if ((rc = ensure(c, c->views, sizeof(ecc::ViewRec) * (size_t)n_views, "views")) != ECC_OK) return rc;
   const size_t tbytes = sizeof(ecc::RadonRow) * (size_t)n_views * n_alpha + sizeof(ecc::RadonView) * (size_t)n_views;
   if ((rc = ensure(c, c->rtable, tbytes, "radon table")) != ECC_OK) return rc;
-  const size_t plane = ecc::radon_plane_floats(W, H, n_s);
+  const size_t plane = ecc::radon_plane_bytes(W, H, n_s);
   const size_t max_batch_bytes = (size_t)256 << 20;
-  int batch = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_views, max_batch_bytes / (plane * 4)));
-  if ((rc = ensure(c, c->wimg, plane * 4 * (size_t)batch, "weighted images")) != ECC_OK) return rc;
+  int batch = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_views, max_batch_bytes / plane));
+  if ((rc = ensure(c, c->wimg, plane * (size_t)batch, "weighted images")) != ECC_OK) return rc;
   if (dtype == ECC_F16 &&
       (rc = ensure(c, c->stage, ecc::radon_f16_stage_bytes(n_alpha, n_s, batch), "FP16 staging")) != ECC_OK)
     return rc;
@@ -175,7 +175,7 @@ int run_precompute(ecc_ctx* c, int n_views, const double* P, const float* images
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "view set-up launch");
   e = ecc::launch_radon((const ecc::ViewRec*)c->views.p, n_views, images, W, H, n_alpha, n_s, dtype, sino_out,
-                        scales_out, (ecc::RadonRow*)c->rtable.p, (float*)c->wimg.p, (float*)c->stage.p, batch, hk, s);
+                        scales_out, (ecc::RadonRow*)c->rtable.p, c->wimg.p, (float*)c->stage.p, batch, hk, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "radon launch");
   return ECC_OK;
 }

@@ -49,11 +49,12 @@ struct LaunchHooks {
 
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_radon(const ViewRec* views, int n_views, const float* images, int W, int H, int n_alpha, int n_s,
-                         int dtype, void* sino_out, float* scales_out, RadonRow* table, float* wimg, float* stage,
+                         int dtype, void* sino_out, float* scales_out, RadonRow* table, void* wimg, float* stage,
                          int batch_views, const LaunchHooks& hooks, cudaStream_t stream);
 size_t radon_f16_stage_bytes(int n_alpha, int n_s, int batch_views);
 int radon_pad(int W, int H, int n_s);
-size_t radon_plane_floats(int W, int H, int n_s);
+// Bytes of one view's weighted-image planes (interpolation pairs, both orientations).
+size_t radon_plane_bytes(int W, int H, int n_s);
 
 cudaError_t launch_ecc_pairs(long long n_pairs, const PairRec* prs, const double2* ctile, int n_tiles,
                              const double2* alpha_dir, const void* sino, const float* scales, int dtype,

@@ -6,18 +6,21 @@
 //                        as 32.32 fixed-point coordinates along the interpolation
 //                        axis (exact integer stepping, no FP64 in the hot loop).
 //   weight_kernel        cosine pre-weight g D / sqrt(D^2 + u^2 + v^2) of each
-//                        projection, written twice: row-major and transposed, each
-//                        with two zero columns of padding on both sides, so that
-//                        every Joseph step reads two adjacent floats of one row.
-//   joseph_kernel        one warp per (view, alpha, 32 consecutive sigma): Joseph
+//                        projection, stored as interpolation pairs (v[i],
+//                        v[i+1] - v[i]) twice: along image rows and along image
+//                        columns, each with a zero margin on both sides wide enough
+//                        for the 32 lines of a warp.
+//   joseph_kernel        one warp per (view, alpha, 31 consecutive s_n), a block's
+//                        warps on consecutive alpha rows (shared image band): Joseph
 //                        line sums (step over rows for |cos a| >= |sin a|, else over
-//                        columns, linear interpolation along the other axis).  The
-//                        half-step difference in s is formed tap by tap between
-//                        neighbouring lanes (warp shuffle) so that it never cancels
-//                        two large FP32 sums (block sums of the differences are
-//                        Kahan-compensated); the (D^2 + s^2)/D^2 weight is applied
-//                        at the end.  Lanes read consecutive floats of one image
-//                        row: coalesced, L1/L2 resident.
+//                        columns, linear interpolation along the other axis), one
+//                        8-byte pair load and one FMA per tap.  The half-step
+//                        difference in s is formed between neighbouring lanes (warp
+//                        shuffle) on 8-row partial sums, so that it never cancels
+//                        two large FP32 sums (Kahan-compensated across blocks); the
+//                        (D^2 + s^2)/D^2 weight is applied at the end.  Lanes read
+//                        consecutive pairs of one image row: coalesced, L1/L2
+//                        resident.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -73,68 +76,127 @@ __global__ void radon_table_kernel(const ViewRec* __restrict__ views, int n_view
   }
 }
 
-// Weighted projection, row-major [H][W + 2 pad] and transposed [W][H + 2 pad]
-// (data from column / row pad, zeros elsewhere).  Block (32, 8) over a 32x32 tile;
-// the transpose goes through shared memory so both writes are coalesced.
+// Weighted projection as interpolation pairs (v[i], v[i+1] - v[i]) along the
+// interpolation axis: row-major [H][pitch_r] (pairs along x) and transposed
+// [W][pitch_c] (pairs along y), the image from element pad on, zeros elsewhere
+// (the pair before the image carries (0, v[0])).  A block (32, 8) covers 32x32
+// pairs starting one pixel before the image; the weighted values of a 33x33 tile
+// are computed once into shared memory and both planes are written coalesced.
 __global__ void weight_kernel(const float* __restrict__ images, const RadonView* __restrict__ rv, int W, int H,
-                              int pad, float* __restrict__ wimg, size_t plane) {
-  __shared__ float tile[32][33];
+                              int pad, int pitch_r, int pitch_c, float2* __restrict__ wimg, size_t plane) {
+  __shared__ float tile[33][34];
   const int v = blockIdx.z;
   const float* g = images + (size_t)v * W * H;
-  float* R = wimg + (size_t)v * plane;
-  float* T = R + (size_t)H * (W + 2 * pad);
+  float2* R = wimg + (size_t)v * plane;
+  float2* T = R + (size_t)H * pitch_r;
   const RadonView r = rv[v];
-  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
-  for (int j = 0; j < 4; ++j) {
-    const int x = bx + threadIdx.x, y = by + threadIdx.y + 8 * j;
+  const int bx = (int)blockIdx.x * 32 - 1, by = (int)blockIdx.y * 32 - 1;
+  for (int i = threadIdx.y * 32 + threadIdx.x; i < 33 * 33; i += 256) {
+    const int ty = i / 33, tx = i % 33;
+    const int x = bx + tx, y = by + ty;
     float w = 0.0f;
-    if (x < W && y < H) {
+    if (x >= 0 && x < W && y >= 0 && y < H) {
       const float du = (float)x - r.u0, dv = (float)y - r.v0;
       w = g[(size_t)y * W + x] * (r.D / sqrtf(r.D * r.D + du * du + dv * dv));
-      R[(size_t)y * (W + 2 * pad) + x + pad] = w;
     }
-    tile[threadIdx.y + 8 * j][threadIdx.x] = w;
+    tile[ty][tx] = w;
   }
   __syncthreads();
   for (int j = 0; j < 4; ++j) {
-    const int xo = bx + threadIdx.y + 8 * j, yo = by + threadIdx.x;
-    if (xo < W && yo < H) T[(size_t)xo * (H + 2 * pad) + yo + pad] = tile[threadIdx.x][threadIdx.y + 8 * j];
+    const int tx = threadIdx.x, ty = threadIdx.y + 8 * j;
+    const int x = bx + tx, y = by + ty;
+    // pairs along x for image rows
+    if (y >= 0 && y < H && x >= -1 && x < W)
+      R[(size_t)y * pitch_r + x + pad] = make_float2(tile[ty][tx], tile[ty][tx + 1] - tile[ty][tx]);
+    // pairs along y for image columns (threads run along y: coalesced)
+    const int xo = bx + ty, yo = by + tx;
+    if (xo >= 0 && xo < W && yo >= -1 && yo < H)
+      T[(size_t)xo * pitch_c + yo + pad] = make_float2(tile[tx][ty], tile[tx + 1][ty] - tile[tx][ty]);
   }
 }
 
-template <typename OutT>
-__device__ __forceinline__ void store_out(OutT* p, float v);
-template <>
-__device__ __forceinline__ void store_out<float>(float* p, float v) { *p = v; }
-template <>
-__device__ __forceinline__ void store_out<__half>(__half* p, float v) { *p = __float2half_rn(v); }
-template <>
-__device__ __forceinline__ void store_out<__nv_bfloat16>(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+// ---------------------------------------------------------------- Joseph line sums
+//
+// One warp per (view, alpha row, 31 consecutive s_n): lane i follows the line at
+// the half-step offset s_{k0+i} - ds/2 (lane 31 provides the line after the last
+// output).  The weighted image is stored as pairs (v[i], v[i+1] - v[i]) along the
+// interpolation axis, so one tap is one 8-byte load and one FMA; lanes read
+// consecutive pairs of one image row (coalesced, L1-resident).  A warp walks only
+// the image rows where some of its lines meet the image (exact row range), in
+// blocks of 16 rows: exact 32.32 fixed-point position at the block's first row,
+// then FP32 offsets u * dy (|u| < 16, error < 2e-6 px); floor and element offset
+// come from one round-down add against 1.5 * 2^23 + u * pitch.  Taps are summed
+// over 8 rows, and the 8-row sum's difference to the next lane's line is added to
+// a Kahan-compensated accumulator, so the half-step difference in s never cancels
+// two large FP32 sums.
+constexpr int kRowsPerAnchor = 16;
+constexpr int kRowsPerBlock = 8;
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23: float ulp 1 for [2^23, 2^24)
+constexpr unsigned kMagicBits = 0x4B400000u;
+constexpr int kMaxPad = 160;  // wider margins: clamped variant
 
-// CLAMP = false: the zero margin (pad) is wider than the span of a warp's 32 lines
-// plus the step-range margins, so every tap read stays inside the padded row
-// without clamping.  CLAMP = true (coarse s grids): pad = 2 and the coordinate is
-// clamped onto the zero columns.
-template <typename OutT, bool CLAMP>
-__global__ void __launch_bounds__(256) joseph_kernel(const RadonRow* __restrict__ table,
-                                                     const RadonView* __restrict__ rv,
-                                                     const float* __restrict__ wimg, size_t plane, int W, int H,
-                                                     int pad, int n_alpha, int n_s, float ds, int warps_per_block,
-                                                     OutT* __restrict__ out) {
+__device__ __forceinline__ void kahan_add(float q, float& acc, float& comp) {
+  const float y = q - comp;
+  const float t = acc + y;
+  comp = (t - acc) - y;
+  acc = t;
+}
+
+constexpr int kAlphaPerBlock = 8;  // warps per block
+
+struct JosephArgs {
+  int W, H, n_alpha, n_s;
+  int pad, pitch_r, pitch_c;  // float2 elements
+  size_t plane;               // float2 elements per view
+  float ds;
+};
+
+// Taps of rows u in [ua, ub) of one anchor block (all 16 rows when FULL).
+template <bool CLAMP, bool FULL>
+__device__ __forceinline__ void joseph_block(uint64_t rp, float f0, float dyf, float lo_c, float hi_c,
+                                             const float (&Mu)[kRowsPerAnchor], int ua, int ub, float& acc,
+                                             float& comp) {
+#pragma unroll
+  for (int i = 0; i < kRowsPerAnchor / kRowsPerBlock; ++i) {
+    float s = 0.0f;
+#pragma unroll
+    for (int uu = 0; uu < kRowsPerBlock; ++uu) {
+      const int u = i * kRowsPerBlock + uu;
+      if (FULL || (u >= ua && u < ub)) {
+        float xf = fmaf((float)u, dyf, f0);
+        if (CLAMP) xf = fminf(fmaxf(xf, lo_c), hi_c);
+        const float t = __fadd_rd(xf, Mu[u]);
+        const float f = xf - (t - Mu[u]);
+        const float2 vd = __ldg(reinterpret_cast<const float2*>(rp + 8ull * __float_as_uint(t)));
+        s += fmaf(f, vd.y, vd.x);
+      }
+    }
+    const float nb = __shfl_down_sync(0xffffffffu, s, 1);
+    kahan_add(nb - s, acc, comp);
+  }
+}
+
+template <bool CLAMP>
+__global__ void __launch_bounds__(32 * kAlphaPerBlock) joseph_kernel(const RadonRow* __restrict__ table,
+                                                                      const RadonView* __restrict__ rv,
+                                                                      const float2* __restrict__ wimg, JosephArgs g,
+                                                                      float* __restrict__ out_f32,
+                                                                      __nv_bfloat16* __restrict__ out_bf16) {
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int v = blockIdx.z, m = blockIdx.y;
-  const int chunk = blockIdx.x * warps_per_block + warp;
-  const int k0 = 31 * chunk;
-  if (k0 >= n_s) return;  // warp-uniform
+  // the warps of a block take the same 31 outputs of consecutive alpha rows: their
+  // image bands largely overlap and are shared through L1
+  const int v = blockIdx.z, m = (int)blockIdx.y * kAlphaPerBlock + warp;
+  if (m >= g.n_alpha) return;  // warp-uniform
+  const int k0 = 31 * (int)blockIdx.x;
   const int k = k0 + lane;
-  const RadonRow row = table[(size_t)v * n_alpha + m];
+  const RadonRow row = table[(size_t)v * g.n_alpha + m];
   const bool rows = row.rows_mode != 0;
-  const float* img = wimg + (size_t)v * plane + (rows ? 0 : (size_t)H * (W + 2 * pad));
-  const int pitch = rows ? W + 2 * pad : H + 2 * pad;
-  const int n_steps = rows ? H : W;
-  const int limit = rows ? W : H;
-  // steps where some lane of the warp is inside the interpolation support
+  const float2* img = wimg + (size_t)v * g.plane + (rows ? 0 : (size_t)g.H * g.pitch_r);
+  const int pitch = rows ? g.pitch_r : g.pitch_c;
+  const int n_steps = rows ? g.H : g.W;
+  const int limit = rows ? g.W : g.H;
+  // image rows where some lane of the warp is inside the interpolation support
   int s_lo = 0, s_hi = n_steps;
   {
     const float scale = 1.0f / 65536.0f;
@@ -144,7 +206,7 @@ __global__ void __launch_bounds__(256) joseph_kernel(const RadonRow* __restrict_
     const float mn = fminf(xa, xb) - 2.0f, mx = fmaxf(xa, xb) + 2.0f;
     const float lo_t = -1.0f, hi_t = (float)limit;
     if (fabsf(dy) > 1e-6f) {
-      float s1 = (lo_t - mx) / dy, s2 = (hi_t - mn) / dy;
+      const float s1 = (lo_t - mx) / dy, s2 = (hi_t - mn) / dy;
       // clamp in float first: nearly axis-parallel lines give huge bounds
       const float cap = (float)n_steps + 4.0f;
       const float sl = fminf(fmaxf(fminf(s1, s2), -4.0f), cap);
@@ -156,58 +218,37 @@ __global__ void __launch_bounds__(256) joseph_kernel(const RadonRow* __restrict_
     }
     if (s_hi < s_lo) s_hi = s_lo;
   }
-  long long X = row.B0 + (long long)k * row.STEP + (long long)s_lo * row.DY;
-  const float* base = img + (size_t)s_lo * pitch + pad;
-  // Each step: tap t_j of this lane's line, t_{j+1} of the neighbour's (next sigma)
-  // by shuffle, and their difference, which is small and (for neighbouring taps of
-  // a smooth image) exact in FP32.  Differences are summed in 8-step blocks; the
-  // block sums are added with Kahan compensation.
-  float q = 0.0f, acc = 0.0f, comp = 0.0f;
-  int s = s_lo;
-  for (; s + 8 <= s_hi; s += 8) {
+  const float dyf = (float)((double)row.DY * (1.0 / 4294967296.0));
+  const long long DY16 = (long long)kRowsPerAnchor * row.DY;
+  float Mu[kRowsPerAnchor];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      int xi = (int)(X >> 32);
-      const unsigned lo = (unsigned)(X & 0xffffffffLL);
-      const float f = __uint_as_float(0x3f800000u | (lo >> 9)) - 1.0f;
-      if (CLAMP) xi = min(max(xi, -2), limit);
-      const float* rp = base + xi;
-      const float v0 = __ldg(rp), v1 = __ldg(rp + 1);
-      const float t = fmaf(f, v1 - v0, v0);
-      const float nb = __shfl_down_sync(0xffffffffu, t, 1);
-      q += nb - t;
-      X += row.DY;
-      base += pitch;
-    }
-    const float y = q - comp;
-    const float tt = acc + y;
-    comp = (tt - acc) - y;
-    acc = tt;
-    q = 0.0f;
+  for (int u = 0; u < kRowsPerAnchor; ++u) Mu[u] = kMagic + (float)(u * pitch);
+  long long X = row.B0 + (long long)k * row.STEP + (long long)s_lo * row.DY;
+  float acc = 0.0f, comp = 0.0f;
+  const uint64_t img_b = reinterpret_cast<uint64_t>(img) - 8ull * kMagicBits;
+  for (int j0 = s_lo; j0 < s_hi; j0 += kRowsPerAnchor) {
+    const int xi0 = (int)(X >> 32);
+    const float f0 = __uint_as_float(0x3f800000u | ((unsigned)X >> 9)) - 1.0f;
+    const uint64_t rp = img_b + 8ull * (uint64_t)((long long)j0 * pitch + g.pad + xi0);
+    const float lo_c = (float)(-2 - xi0), hi_c = (float)(limit - xi0);
+    const int n = s_hi - j0;
+    if (n >= kRowsPerAnchor)
+      joseph_block<CLAMP, true>(rp, f0, dyf, lo_c, hi_c, Mu, 0, n, acc, comp);
+    else
+      joseph_block<CLAMP, false>(rp, f0, dyf, lo_c, hi_c, Mu, 0, n, acc, comp);
+    X += DY16;
   }
-  for (; s < s_hi; ++s) {
-    int xi = (int)(X >> 32);
-    const unsigned lo = (unsigned)(X & 0xffffffffLL);
-    const float f = __uint_as_float(0x3f800000u | (lo >> 9)) - 1.0f;
-    if (CLAMP) xi = min(max(xi, -2), limit);
-    const float* rp = base + xi;
-    const float v0 = __ldg(rp), v1 = __ldg(rp + 1);
-    const float t = fmaf(f, v1 - v0, v0);
-    const float nb = __shfl_down_sync(0xffffffffu, t, 1);
-    q += nb - t;
-    X += row.DY;
-    base += pitch;
-  }
-  {
-    const float y = q - comp;
-    acc = acc + y;
-  }
-  if (lane < 31 && k < n_s) {
+  if (lane < 31 && k < g.n_s) {
     const RadonView r = rv[v];
-    const float sn = ((float)k - 0.5f * (float)(n_s - 1)) * ds;
-    const float spp = sn - (r.u0 - 0.5f * (float)(W - 1)) * row.ca - (r.v0 - 0.5f * (float)(H - 1)) * row.sa;
+    const float sn = ((float)k - 0.5f * (float)(g.n_s - 1)) * g.ds;
+    const float spp = sn - (r.u0 - 0.5f * (float)(g.W - 1)) * row.ca - (r.v0 - 0.5f * (float)(g.H - 1)) * row.sa;
     const float wgt = (r.D * r.D + spp * spp) / (r.D * r.D);
-    store_out<OutT>(out + ((size_t)v * n_alpha + m) * n_s + k, acc * (row.inv_len / ds) * wgt);
+    const float val = (acc - comp) * (row.inv_len / g.ds) * wgt;
+    const size_t o = ((size_t)v * g.n_alpha + m) * g.n_s + k;
+    if (out_bf16)
+      out_bf16[o] = __float2bfloat16_rn(val);
+    else
+      out_f32[o] = val;
   }
 }
 
@@ -239,16 +280,15 @@ __global__ void quantize_f16_kernel(const float* __restrict__ s32, size_t per_vi
 
 int radon_pad(int W, int H, int n_s) {
   // span of 32 neighbouring lines along the interpolation axis (|cos| or |sin| >=
-  // 1/sqrt 2 in their mode) plus the margins of the per-warp step range
+  // 1/sqrt 2 in their mode) plus the margins of the per-warp row range
   const double ds = sqrt((double)W * W + (double)H * H) / (n_s - 1);
   const int need = (int)ceil(31.0 * ds * 1.41421356237309515 + 8.0);
-  const int pad = (need + 3) / 4 * 4;
-  return pad <= 160 ? pad : 2;  // 2: clamped variant
+  return need <= kMaxPad ? need : 2;  // 2: clamped variant
 }
 
-size_t radon_plane_floats(int W, int H, int n_s) {
+size_t radon_plane_bytes(int W, int H, int n_s) {
   const int pad = radon_pad(W, H, n_s);
-  return (size_t)H * (W + 2 * pad) + (size_t)W * (H + 2 * pad);
+  return sizeof(float2) * ((size_t)H * (W + 2 * pad) + (size_t)W * (H + 2 * pad));
 }
 
 size_t radon_f16_stage_bytes(int n_alpha, int n_s, int batch_views) {
@@ -256,7 +296,7 @@ size_t radon_f16_stage_bytes(int n_alpha, int n_s, int batch_views) {
 }
 
 cudaError_t launch_radon(const ViewRec* views, int n_views, const float* images, int W, int H, int n_alpha, int n_s,
-                         int dtype, void* sino_out, float* scales_out, RadonRow* table, float* wimg,
+                         int dtype, void* sino_out, float* scales_out, RadonRow* table, void* wimg,
                          float* stage, int batch_views, const LaunchHooks& hooks, cudaStream_t stream) {
   // table and per-view weights (RadonView array sits right after the table)
   RadonView* rv = reinterpret_cast<RadonView*>(table + (size_t)n_views * n_alpha);
@@ -269,47 +309,42 @@ cudaError_t launch_radon(const ViewRec* views, int n_views, const float* images,
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  const int pad = radon_pad(W, H, n_s);
-  const bool clamp = pad == 2;
-  const size_t plane = radon_plane_floats(W, H, n_s);
-  const float ds = (float)(sqrt((double)W * W + (double)H * H) / (n_s - 1));
+  JosephArgs jg;
+  jg.W = W;
+  jg.H = H;
+  jg.n_alpha = n_alpha;
+  jg.n_s = n_s;
+  jg.pad = radon_pad(W, H, n_s);
+  const bool clamp = jg.pad == 2;
+  jg.pitch_r = W + 2 * jg.pad;
+  jg.pitch_c = H + 2 * jg.pad;
+  jg.plane = radon_plane_bytes(W, H, n_s) / sizeof(float2);
+  jg.ds = (float)(sqrt((double)W * W + (double)H * H) / (n_s - 1));
   const int n_chunks = (n_s + 30) / 31;
-  const int blocks_x = (n_chunks + 7) / 8;
-  const int wpb = (n_chunks + blocks_x - 1) / blocks_x;
+  float2* wv = reinterpret_cast<float2*>(wimg);
   for (int v0 = 0; v0 < n_views; v0 += batch_views) {
     const int nb = min(batch_views, n_views - v0);
-    cudaError_t e = cudaMemsetAsync(wimg, 0, sizeof(float) * plane * nb, stream);
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
+    if (v0 == 0) {  // zero margins; later batches overwrite only the pairs of the image
+      e = cudaMemsetAsync(wimg, 0, sizeof(float2) * jg.plane * nb, stream);
+      if (e != cudaSuccess) return e;
+    }
     hooks.on_begin("weight_kernel", stream);
-    weight_kernel<<<dim3((W + 31) / 32, (H + 31) / 32, nb), dim3(32, 8), 0, stream>>>(
-        images + (size_t)v0 * W * H, rv + v0, W, H, pad, wimg, plane);
+    weight_kernel<<<dim3((W + 32) / 32, (H + 32) / 32, nb), dim3(32, 8), 0, stream>>>(
+        images + (size_t)v0 * W * H, rv + v0, W, H, jg.pad, jg.pitch_r, jg.pitch_c, wv, jg.plane);
     hooks.on_end("weight_kernel", stream);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const dim3 grid(blocks_x, n_alpha, nb), block(32 * wpb);
     const RadonRow* tb = table + (size_t)v0 * n_alpha;
+    const size_t oo = (size_t)v0 * n_alpha * n_s;
+    float* of = dtype == 0 ? (float*)sino_out + oo : (dtype == 1 ? stage : nullptr);
+    __nv_bfloat16* ob = dtype == 2 ? (__nv_bfloat16*)sino_out + oo : nullptr;
+    const dim3 grid(n_chunks, (n_alpha + kAlphaPerBlock - 1) / kAlphaPerBlock, nb), block(32 * kAlphaPerBlock);
     hooks.on_begin("joseph_kernel", stream);
-#define JOSEPH(OT, OUTPTR)                                                                                    \
-  do {                                                                                                      \
-    if (clamp)                                                                                              \
-      joseph_kernel<OT, true><<<grid, block, 0, stream>>>(tb, rv + v0, wimg, plane, W, H, pad, n_alpha, n_s, \
-                                                          ds, wpb, OUTPTR);                                   \
-    else                                                                                                    \
-      joseph_kernel<OT, false><<<grid, block, 0, stream>>>(tb, rv + v0, wimg, plane, W, H, pad, n_alpha, n_s, \
-                                                           ds, wpb, OUTPTR);                                  \
-  } while (0)
-    switch (dtype) {
-      case 0:
-        JOSEPH(float, (float*)sino_out + (size_t)v0 * n_alpha * n_s);
-        break;
-      case 1:  // FP32 into the staging buffer; scaled and rounded to FP16 below
-        JOSEPH(float, stage);
-        break;
-      default:
-        JOSEPH(__nv_bfloat16, (__nv_bfloat16*)sino_out + (size_t)v0 * n_alpha * n_s);
-        break;
-    }
-#undef JOSEPH
+    if (clamp)
+      joseph_kernel<true><<<grid, block, 0, stream>>>(tb, rv + v0, wv, jg, of, ob);
+    else
+      joseph_kernel<false><<<grid, block, 0, stream>>>(tb, rv + v0, wv, jg, of, ob);
     hooks.on_end("joseph_kernel", stream);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
