@@ -200,6 +200,68 @@ int ecc_scan_consistency_host(ecc_ctx* ctx, int n_views, const double* P_host, c
                               void* stream);
 
 /*
+ * Serving: motion-compensation jobs by continuous batching (not in the paper; the
+ * paper's motion estimate minimises Eq. 17 over the per-view motion of the
+ * Optimization section).  A job is one scan: its dRadon/ds precompute (as
+ * ecc_precompute_radon_derivative), then n_iters gradient steps
+ *   theta <- theta - step * d total / d theta   (as ecc_evaluate_grad, all a < b)
+ * and a final evaluation at the last theta.  The context runs two threads: one
+ * admits queued jobs in arrival order while the job's device memory fits the
+ * serving budget (the context's hbm_budget_bytes, or 80 % of the device memory
+ * free at the first ecc_submit when that is 0) and runs its precompute; the other
+ * runs rounds in which every admitted job does one iteration.  A round's pair work
+ * of all jobs is one persistent launch; jobs join and leave between rounds.  A
+ * job's results do not depend on the other jobs in its rounds (every reduction has
+ * a fixed order per job).
+ *
+ * The host arrays a job points to (P, motion0, images, motion_out, totals_out) must
+ * stay valid until ecc_poll has returned something other than ECC_EPENDING for its
+ * ticket.  Pinned host memory makes the input copies asynchronous.  While jobs are
+ * served, the context may still be used for the other calls from its own thread.
+ */
+typedef struct ecc_job {
+  int n_views;              /* >= 2 (<= 4096) */
+  const double* P;          /* host FP64 [n_views][12] */
+  const double* motion0;    /* host FP64 [n_views][6] initial theta, or NULL (zeros) */
+  const float* images;      /* host FP32 [n_views][H][W] */
+  int W, H, n_alpha, n_s;   /* detector and dRadon/ds grid (limits as the precompute) */
+  int dtype;                /* sinogram storage: ECC_F32, ECC_F16 or ECC_BF16 */
+  int n_kappa;              /* planes per pair (1 .. 65536) */
+  double cauchy_c;          /* Eq. 16 (<= 0: none) */
+  int n_iters;              /* gradient steps (>= 0) */
+  double step;              /* step size */
+  double* motion_out;       /* host FP64 [n_views][6] final theta, or NULL */
+  double* totals_out;       /* host FP64 [n_iters + 1] total at theta_0 .. theta_n, or NULL */
+} ecc_job;
+
+typedef struct ecc_result {
+  int status;               /* ECC_OK or the error that ended the job */
+  int iters;                /* gradient steps taken */
+  double total_first;       /* total at theta_0 */
+  double total_last;        /* total at the final theta */
+  double queue_ms;          /* ecc_submit -> admission */
+  double latency_ms;        /* ecc_submit -> results in host memory */
+  size_t footprint_bytes;   /* device memory held while admitted (precompute peak) */
+  long long line_pairs;     /* line-pair samples evaluated: pairs x n_kappa x (n_iters + 1) */
+} ecc_result;
+
+/* Device memory a job needs at admission (ECC_EINVAL for an invalid job). */
+int ecc_job_footprint(const ecc_job* job, size_t* bytes);
+
+/* Queues a job and returns its ticket.  ECC_EADMIT if the job can never fit the
+ * serving budget; ECC_EINVAL for an invalid job. */
+int ecc_submit(ecc_ctx* ctx, const ecc_job* job, uint64_t* ticket);
+
+/* ECC_EPENDING while the job is queued or running.  Otherwise fills *out (if not
+ * NULL), forgets the ticket and returns the job's status (ECC_OK, or the error that
+ * ended it; the message is then in ecc_last_error).  ECC_EINVAL: unknown ticket. */
+int ecc_poll(ecc_ctx* ctx, uint64_t ticket, ecc_result* out);
+
+/* Serving counters since the first ecc_submit: rounds run, sum over rounds of the
+ * jobs in them, the largest round, and the line-pair samples of completed jobs. */
+int ecc_serve_stats(ecc_ctx* ctx, long long* rounds, long long* job_rounds, int* max_batch, long long* line_pairs);
+
+/*
  * Allocation-free ecc_evaluate.  The paper has no counterpart: this is a service of
  * the library, not a step of the method.  It computes exactly what ecc_evaluate
  * computes, with the same arguments minus the context, for callers that must not

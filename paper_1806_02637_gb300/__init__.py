@@ -24,13 +24,29 @@ from . import build as _build
 __all__ = ["EccError", "Context", "library_path", "load", "ecc_precompute_radon_derivative", "ecc_evaluate",
            "ecc_evaluate_grad", "ecc_evaluate_frozen", "ecc_evaluate_noalloc", "consistency",
            "ecc_scan_consistency_host", "ecc_status", "ecc_kernel_launches", "ecc_profile_enable",
-           "ecc_profile_read", "ECC_F32", "ECC_F16", "ECC_BF16"]
+           "ecc_profile_read", "ecc_job_footprint", "ecc_submit", "ecc_poll", "ecc_serve_stats",
+           "ECC_F32", "ECC_F16", "ECC_BF16"]
 
 ECC_F32, ECC_F16, ECC_BF16 = 0, 1, 2
 ECC_OK = 0
 
 _lock = threading.Lock()
 _lib = None
+ECC_EPENDING = 1
+
+
+class _Job(ctypes.Structure):
+    _fields_ = [("n_views", ctypes.c_int), ("P", ctypes.c_void_p), ("motion0", ctypes.c_void_p),
+                ("images", ctypes.c_void_p), ("W", ctypes.c_int), ("H", ctypes.c_int), ("n_alpha", ctypes.c_int),
+                ("n_s", ctypes.c_int), ("dtype", ctypes.c_int), ("n_kappa", ctypes.c_int),
+                ("cauchy_c", ctypes.c_double), ("n_iters", ctypes.c_int), ("step", ctypes.c_double),
+                ("motion_out", ctypes.c_void_p), ("totals_out", ctypes.c_void_p)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("total_first", ctypes.c_double),
+                ("total_last", ctypes.c_double), ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
+                ("footprint_bytes", ctypes.c_size_t), ("line_pairs", ctypes.c_longlong)]
 
 
 class EccError(RuntimeError):
@@ -82,6 +98,15 @@ def load(build_if_missing: bool = True):
         lib.ecc_profile_read.argtypes = [vp, vp, i, ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong),
                                          ctypes.POINTER(d), ctypes.POINTER(i)]
         lib.ecc_profile_read.restype = i
+        lib.ecc_job_footprint.argtypes = [ctypes.POINTER(_Job), ctypes.POINTER(sz)]
+        lib.ecc_job_footprint.restype = i
+        lib.ecc_submit.argtypes = [vp, ctypes.POINTER(_Job), ctypes.POINTER(ctypes.c_uint64)]
+        lib.ecc_submit.restype = i
+        lib.ecc_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(_Result)]
+        lib.ecc_poll.restype = i
+        lib.ecc_serve_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                        ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong)]
+        lib.ecc_serve_stats.restype = i
         _lib = lib
         return lib
 
@@ -141,6 +166,7 @@ class Context:
             raise EccError(f"ecc_create failed ({rc}): {msg.decode() if msg else ''}")
         self.handle = h
         self.device = int(device)
+        self._jobs = {}  # ticket -> host arrays of a served job (kept alive until polled)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -396,3 +422,87 @@ def ecc_profile_read(ctx: Context, stream=None, max_entries: int = 32) -> dict:
         nm = names.raw[32 * k:32 * (k + 1)].split(b"\0", 1)[0].decode()
         out[nm] = (int(launches[k]), float(ms[k]))
     return out
+
+
+# ---------------------------------------------------------------- serving
+_DT = {"float32": ECC_F32, "float16": ECC_F16, "bfloat16": ECC_BF16}
+
+
+def _host_array(a, dtype, name, shape):
+    """Host array for a job: numpy or CPU torch tensor (pinned memory is used as is)."""
+    torch = _torch()
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda:
+            raise EccError(f"{name} must be in host memory")
+        if a.dtype != getattr(torch, np.dtype(dtype).name) or not a.is_contiguous():
+            raise EccError(f"{name} must be a contiguous {np.dtype(dtype).name} tensor")
+        ptr = a.data_ptr()
+    else:
+        a = np.ascontiguousarray(a, dtype=dtype)
+        ptr = a.ctypes.data
+    if tuple(a.shape) != tuple(shape):
+        raise EccError(f"{name} has shape {tuple(a.shape)}, expected {tuple(shape)}")
+    return a, ptr
+
+
+def _job_struct(P, images, W, H, n_alpha, n_s, n_kappa, n_iters, step, dtype, cauchy_c, motion0):
+    n = int(P.shape[0])
+    P, p_ptr = _host_array(P, np.float64, "P", (n, 3, 4))
+    images, i_ptr = _host_array(images, np.float32, "images", (n, H, W))
+    m_ptr = None
+    if motion0 is not None:
+        motion0, m_ptr = _host_array(motion0, np.float64, "motion0", (n, 6))
+    code = _DT[dtype] if isinstance(dtype, str) else _dtype_code(dtype)
+    motion_out = np.zeros((n, 6))
+    totals_out = np.zeros(int(n_iters) + 1)
+    j = _Job(n, p_ptr, m_ptr, i_ptr, int(W), int(H), int(n_alpha), int(n_s), code, int(n_kappa), float(cauchy_c),
+             int(n_iters), float(step), motion_out.ctypes.data, totals_out.ctypes.data)
+    return j, (P, images, motion0, motion_out, totals_out)
+
+
+def ecc_job_footprint(P, images, W: int, H: int, n_alpha: int, n_s: int, n_kappa: int, n_iters: int = 20,
+                      step: float = 0.0, dtype="float32", cauchy_c: float = 0.0, motion0=None) -> int:
+    """Device bytes the job holds while admitted."""
+    j, _ = _job_struct(P, images, W, H, n_alpha, n_s, n_kappa, n_iters, step, dtype, cauchy_c, motion0)
+    b = ctypes.c_size_t(0)
+    rc = load().ecc_job_footprint(ctypes.byref(j), ctypes.byref(b))
+    _check(None, rc, "ecc_job_footprint")
+    return int(b.value)
+
+
+def ecc_submit(ctx: Context, P, images, W: int, H: int, n_alpha: int, n_s: int, n_kappa: int, n_iters: int = 20,
+               step: float = 0.0, dtype="float32", cauchy_c: float = 0.0, motion0=None) -> int:
+    """Queues a motion-compensation job (host P [n,3,4] float64, images [n,H,W] float32,
+    optional motion0 [n,6]); returns its ticket.  The host arrays are kept alive by the
+    context until the job is polled."""
+    j, keep = _job_struct(P, images, W, H, n_alpha, n_s, n_kappa, n_iters, step, dtype, cauchy_c, motion0)
+    t = ctypes.c_uint64(0)
+    rc = load().ecc_submit(ctx.handle, ctypes.byref(j), ctypes.byref(t))
+    _check(ctx, rc, "ecc_submit")
+    ctx._jobs[int(t.value)] = keep
+    return int(t.value)
+
+
+def ecc_poll(ctx: Context, ticket: int):
+    """None while the job is pending; otherwise a dict with the result record, the
+    final motion [n,6] and the totals [n_iters + 1] (raises EccError if the job failed)."""
+    r = _Result()
+    rc = load().ecc_poll(ctx.handle, ctypes.c_uint64(ticket), ctypes.byref(r))
+    if rc == ECC_EPENDING:
+        return None
+    keep = ctx._jobs.pop(int(ticket), None)
+    _check(ctx, rc, "ecc_poll")
+    out = {k: getattr(r, k) for k, _ in _Result._fields_}
+    if keep is not None:
+        out["motion"] = keep[3]
+        out["totals"] = keep[4]
+    return out
+
+
+def ecc_serve_stats(ctx: Context) -> dict:
+    rounds, job_rounds, lp = ctypes.c_longlong(0), ctypes.c_longlong(0), ctypes.c_longlong(0)
+    mb = ctypes.c_int(0)
+    rc = load().ecc_serve_stats(ctx.handle, ctypes.byref(rounds), ctypes.byref(job_rounds), ctypes.byref(mb),
+                                ctypes.byref(lp))
+    _check(ctx, rc, "ecc_serve_stats")
+    return {"rounds": rounds.value, "job_rounds": job_rounds.value, "max_batch": mb.value, "line_pairs": lp.value}

@@ -13,6 +13,7 @@
 #include "../../include/ecc.h"
 #include "ecc_internal.cuh"
 #include "kernels.cuh"
+#include "serve.h"
 
 namespace {
 
@@ -47,6 +48,7 @@ struct ecc_ctx {
   int samp_views = 0, samp_pairs = 0, samp_K = 0, samp_W = 0, samp_H = 0;
   const void* samp_pair_ptr = nullptr;
   Buf h_P, h_img, h_sino, h_total;  // buffers of the host-buffer entry point
+  ecc_serve* serve = nullptr;       // serving scheduler, created by the first ecc_submit
 };
 
 namespace {
@@ -304,6 +306,7 @@ int ecc_create(ecc_ctx** out, int device, size_t hbm_budget_bytes) {
 void ecc_destroy(ecc_ctx* c) {
   if (!c) return;
   DeviceGuard g(c->device);
+  ecc::serve_destroy(c->serve);
   cudaDeviceSynchronize();
   Buf* bufs[] = {&c->views, &c->pairs, &c->ctile, &c->adir, &c->perpair, &c->nk, &c->partial, &c->rtable, &c->wimg,
                  &c->vtan, &c->Gpp, &c->gpp, &c->stage, &c->h_P, &c->h_img, &c->h_sino, &c->h_total};
@@ -482,6 +485,49 @@ int ecc_scan_consistency_host(ecc_ctx* c, int n_views, const double* P_host, con
   e = cudaMemcpyAsync(total_host, c->h_total.p, sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
+  return ECC_OK;
+}
+
+int ecc_job_footprint(const ecc_job* job, size_t* bytes) {
+  if (!bytes) return fail(nullptr, ECC_EINVAL, "bytes is NULL");
+  std::string why;
+  const int rc = ecc::serve_footprint(job, bytes, &why);
+  if (rc != ECC_OK) return fail(nullptr, rc, "%s", why.c_str());
+  return ECC_OK;
+}
+
+int ecc_submit(ecc_ctx* c, const ecc_job* job, uint64_t* ticket) {
+  if (!c) return fail(nullptr, ECC_EINVAL, "ctx is NULL");
+  std::string why;
+  if (!c->serve) {
+    DeviceGuard g(c->device);
+    c->serve = ecc::serve_create(c->device, c->budget, &why);
+    if (!c->serve) return fail(c, ECC_ECUDA, "%s", why.c_str());
+  }
+  const int rc = ecc::serve_submit(c->serve, job, ticket, &why);
+  if (rc != ECC_OK) return fail(c, rc, "%s", why.c_str());
+  return ECC_OK;
+}
+
+int ecc_poll(ecc_ctx* c, uint64_t ticket, ecc_result* out) {
+  if (!c) return fail(nullptr, ECC_EINVAL, "ctx is NULL");
+  if (!c->serve) return fail(c, ECC_EINVAL, "no job was submitted on this context");
+  std::string why;
+  const int rc = ecc::serve_poll(c->serve, ticket, out, &why);
+  if (rc < 0) return fail(c, rc, "%s", why.c_str());
+  return rc;
+}
+
+int ecc_serve_stats(ecc_ctx* c, long long* rounds, long long* job_rounds, int* max_batch, long long* line_pairs) {
+  if (!c) return fail(nullptr, ECC_EINVAL, "ctx is NULL");
+  if (!c->serve) {
+    if (rounds) *rounds = 0;
+    if (job_rounds) *job_rounds = 0;
+    if (max_batch) *max_batch = 0;
+    if (line_pairs) *line_pairs = 0;
+    return ECC_OK;
+  }
+  ecc::serve_stats(c->serve, rounds, job_rounds, max_batch, line_pairs);
   return ECC_OK;
 }
 

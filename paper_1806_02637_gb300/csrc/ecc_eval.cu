@@ -264,19 +264,24 @@ __device__ __forceinline__ float sample_grad(const T* __restrict__ sv, int n_alp
   return scale * sign * fmaf(fa, v1 - v0, v0);
 }
 
+// One pair per warp (one plane per lane, tiles of 32): d, e and N_kappa of pair p
+// and, for GRAD, the adjoint d e / d A; returns e on every lane.
 template <typename T, bool GRAD>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-    ecc_pair_kernel(long long n_pairs, const PairRec* __restrict__ prs, const double2* __restrict__ ctile,
-                    int n_tiles, const double2* __restrict__ alpha_dir, const T* __restrict__ sino,
-                    const float* __restrict__ scales, int n_alpha, int n_s, int K, double inv_ds,
-                    float cauchy_c, double* __restrict__ per_pair, int32_t* __restrict__ nk_out,
-                    double* __restrict__ block_partial, double* __restrict__ Gpp) {
-  __shared__ double e_warp[kWarpsPerBlock];
-  const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  const long long p = (long long)blockIdx.x * kWarpsPerBlock + wib;
+__device__ __forceinline__ double pair_warp(const PairArgs& g, long long p, int lane) {
+  const PairRec* __restrict__ prs = g.prs;
+  const double2* __restrict__ ctile = g.ctile;
+  const int n_tiles = g.n_tiles;
+  const double2* __restrict__ alpha_dir = g.alpha_dir;
+  const T* __restrict__ sino = static_cast<const T*>(g.sino);
+  const float* __restrict__ scales = g.scales;
+  const int n_alpha = g.n_alpha, n_s = g.n_s, K = g.K;
+  const double inv_ds = g.inv_ds;
+  const float cauchy_c = g.cauchy_c;
+  double* __restrict__ per_pair = g.per_pair;
+  int32_t* __restrict__ nk_out = g.nk_out;
+  double* __restrict__ Gpp = g.Gpp;
   double e_val = 0.0;
-  if (p < n_pairs) {
+  {
     const PairRec& pr = prs[p];
     const int status = pr.status;
     const int nk = status == 0 ? pr.nk : 0;
@@ -381,19 +386,34 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     }
     e_val = (double)e;
   }
+  return e_val;
+}
+
+// One block of kWarpsPerBlock consecutive pairs: their e summed in a fixed order
+// into partial[blk].
+template <typename T, bool GRAD>
+__device__ __forceinline__ void pair_block(const PairArgs& g, long long blk, double* e_warp) {
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const long long p = blk * kWarpsPerBlock + wib;
+  const double e_val = p < g.n_pairs ? pair_warp<T, GRAD>(g, p, lane) : 0.0;  // warp-uniform
   if (lane == 0) e_warp[wib] = e_val;
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < kWarpsPerBlock; ++w) s += e_warp[w];
-    block_partial[blockIdx.x] = s;
+    g.block_partial[blk] = s;
   }
+  __syncthreads();
 }
 
-// Fixed-order sum of the block partials (one block): deterministic total.
-__global__ void __launch_bounds__(1024) reduce_kernel(const double* __restrict__ partial, int n,
-                                                      double* __restrict__ total) {
-  __shared__ double s[1024];
+template <typename T, bool GRAD>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) ecc_pair_kernel(PairArgs g) {
+  __shared__ double e_warp[kWarpsPerBlock];
+  pair_block<T, GRAD>(g, blockIdx.x, e_warp);
+}
+
+// Fixed-order sum of n block partials by one block of 1024 threads: deterministic.
+__device__ void reduce_fixed(const double* __restrict__ partial, int n, double* __restrict__ total, double* s) {
   double acc = 0.0;
   const int per = (n + blockDim.x - 1) / blockDim.x;
   const int beg = threadIdx.x * per;
@@ -406,6 +426,52 @@ __global__ void __launch_bounds__(1024) reduce_kernel(const double* __restrict__
     __syncthreads();
   }
   if (threadIdx.x == 0) *total = s[0];
+}
+
+__global__ void __launch_bounds__(1024) reduce_kernel(const double* __restrict__ partial, int n,
+                                                      double* __restrict__ total) {
+  __shared__ double s[1024];
+  reduce_fixed(partial, n, total, s);
+}
+
+// Serving: all active jobs' pair blocks in one persistent launch.  Each CTA takes
+// the next block index from a global counter (no waiting on other CTAs), finds its
+// job and runs the same per-block code as the single-scan kernel, so every job's
+// partials, and its total, equal those of an evaluation of the job alone.
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) serve_pair_kernel(const ServeJob* __restrict__ jobs,
+                                                                         const long long* __restrict__ boff,
+                                                                         int n_jobs,
+                                                                         unsigned long long* __restrict__ next) {
+  __shared__ double e_warp[kWarpsPerBlock];
+  __shared__ long long item;
+  const long long total = boff[n_jobs];
+  for (;;) {
+    if (threadIdx.x == 0) item = (long long)atomicAdd(next, 1ull);
+    __syncthreads();
+    const long long it = item;
+    __syncthreads();
+    if (it >= total) return;  // block-uniform
+    const int j = serve_job_of(boff, n_jobs, it);
+    const PairArgs g = jobs[j].pair;
+    const long long blk = it - boff[j];
+    switch (jobs[j].dtype) {
+      case 0:
+        pair_block<float, true>(g, blk, e_warp);
+        break;
+      case 1:
+        pair_block<__half, true>(g, blk, e_warp);
+        break;
+      default:
+        pair_block<__nv_bfloat16, true>(g, blk, e_warp);
+        break;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) serve_reduce_kernel(const ServeJob* __restrict__ jobs) {
+  __shared__ double s[1024];
+  const ServeJob& J = jobs[blockIdx.x];
+  reduce_fixed(J.pair.block_partial, (int)((J.pair.n_pairs + kWarpsPerBlock - 1) / kWarpsPerBlock), J.total_out, s);
 }
 
 }  // namespace
@@ -422,30 +488,59 @@ cudaError_t launch_ecc_pairs(long long n_pairs, const PairRec* prs, const double
   const float cc = (float)cauchy_c;
   const char* name = Gpp ? "ecc_pair_grad_kernel" : "ecc_pair_kernel";
   hooks.on_begin(name, stream);
-#define ECC_LAUNCH(TT, SC)                                                                                       \
-  do {                                                                                                         \
-    if (Gpp)                                                                                                   \
-      ecc_pair_kernel<TT, true><<<grid, block, 0, stream>>>(n_pairs, prs, ctile, n_tiles, alpha_dir,            \
-                                                            (const TT*)sino, SC, n_alpha, n_s, K, inv_ds, cc,  \
-                                                            per_pair, nk_out, block_partial, Gpp);             \
-    else                                                                                                       \
-      ecc_pair_kernel<TT, false><<<grid, block, 0, stream>>>(n_pairs, prs, ctile, n_tiles, alpha_dir,           \
-                                                             (const TT*)sino, SC, n_alpha, n_s, K, inv_ds, cc, \
-                                                             per_pair, nk_out, block_partial, nullptr);        \
+  PairArgs g;
+  g.n_pairs = n_pairs;
+  g.prs = prs;
+  g.ctile = ctile;
+  g.n_tiles = n_tiles;
+  g.alpha_dir = alpha_dir;
+  g.sino = sino;
+  g.scales = dtype == 1 ? scales : nullptr;
+  g.n_alpha = n_alpha;
+  g.n_s = n_s;
+  g.K = K;
+  g.inv_ds = inv_ds;
+  g.cauchy_c = cc;
+  g.per_pair = per_pair;
+  g.nk_out = nk_out;
+  g.block_partial = block_partial;
+  g.Gpp = Gpp;
+#define ECC_LAUNCH(TT)                                                      \
+  do {                                                                      \
+    if (Gpp)                                                                \
+      ecc_pair_kernel<TT, true><<<grid, block, 0, stream>>>(g);             \
+    else                                                                    \
+      ecc_pair_kernel<TT, false><<<grid, block, 0, stream>>>(g);            \
   } while (0)
   switch (dtype) {
     case 0:
-      ECC_LAUNCH(float, nullptr);
+      ECC_LAUNCH(float);
       break;
     case 1:
-      ECC_LAUNCH(__half, scales);
+      ECC_LAUNCH(__half);
       break;
     default:
-      ECC_LAUNCH(__nv_bfloat16, nullptr);
+      ECC_LAUNCH(__nv_bfloat16);
       break;
   }
 #undef ECC_LAUNCH
   hooks.on_end(name, stream);
+  return cudaGetLastError();
+}
+
+int serve_pairs_blocks_per_sm() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, serve_pair_kernel, kWarpsPerBlock * 32, 0) != cudaSuccess)
+    return 1;
+  return n > 0 ? n : 1;
+}
+
+cudaError_t launch_serve_pairs(const ServeJob* jobs, const long long* boff, int n_jobs,
+                               unsigned long long* counter, int grid, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return e;
+  serve_pair_kernel<<<grid, kWarpsPerBlock * 32, 0, stream>>>(jobs, boff, n_jobs, counter);
+  serve_reduce_kernel<<<n_jobs, 1024, 0, stream>>>(jobs);
   return cudaGetLastError();
 }
 

@@ -161,18 +161,15 @@ __global__ void view_setup_kernel(int n_views, const double* __restrict__ P, con
 
 // Tangents of the per-view geometry with respect to the view's own motion
 // parameters (forward mode, FP64): d C / d theta, d up / d theta, d cofc / d theta.
-__global__ void view_tangent_kernel(int n_views, const double* __restrict__ P, const double* __restrict__ motion,
-                                    int W, int H, ViewTan* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_views) return;
+__device__ ViewTan view_tangent(const double* P, const double* motion, int W, int H) {
   using D6 = Dual<6>;
   D6 th[6];
   for (int j = 0; j < 6; ++j) {
-    th[j] = D6(motion ? motion[6 * i + j] : 0.0);
+    th[j] = D6(motion ? motion[j] : 0.0);
     th[j].d[j] = 1.0;
   }
   D6 Pm[12], Pn[12], C[3], up[3], cofc[9], u0, v0, D;
-  moved_projection(P + 12 * i, th, Pm);
+  moved_projection(P, th, Pm);
   view_geometry(Pm, W, H, Pn, C, up, cofc, &u0, &v0, &D);
   ViewTan t;
   for (int j = 0; j < 6; ++j) {
@@ -182,7 +179,14 @@ __global__ void view_tangent_kernel(int n_views, const double* __restrict__ P, c
     }
     for (int k = 0; k < 9; ++k) t.dcofc[k][j] = cofc[k].d[j];
   }
-  out[i] = t;
+  return t;
+}
+
+__global__ void view_tangent_kernel(int n_views, const double* __restrict__ P, const double* __restrict__ motion,
+                                    int W, int H, ViewTan* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_views) return;
+  out[i] = view_tangent(P + 12 * i, motion ? motion + 6 * i : nullptr, W, H);
 }
 
 namespace {
@@ -377,13 +381,8 @@ __global__ void pair_setup_kernel(int n_views, long long n_pairs, const int32_t*
 // views: the frame (w, v) and the kappa -> line maps A = cof(M) [w v] are
 // recomputed with forward-mode tangents (FP64), then contracted with
 // G = d e / d A accumulated by the pair kernel (already scaled by de/dd / N).
-__global__ void pair_grad_kernel(long long n_pairs, const PairRec* __restrict__ prs,
-                                 const ViewRec* __restrict__ views, const ViewTan* __restrict__ vtan,
-                                 const double* __restrict__ Gpp, double* __restrict__ gpp) {
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n_pairs) return;
-  const PairRec& pr = prs[p];
-  double* out = gpp + 12 * p;
+__device__ void pair_grad(const PairRec& pr, const ViewRec* __restrict__ views, const ViewTan* __restrict__ vtan,
+                          const double* __restrict__ G, double* __restrict__ out) {
   if (pr.status != 0 || pr.nk <= 0) {
     for (int j = 0; j < 12; ++j) out[j] = 0.0;
     return;
@@ -411,7 +410,6 @@ __global__ void pair_grad_kernel(long long n_pairs, const PairRec* __restrict__ 
   pencil_frame(C[0], C[1], up[0], up[1], w, v);
   double g[12];
   for (int j = 0; j < 12; ++j) g[j] = 0.0;
-  const double* G = Gpp + 12 * p;
   for (int s = 0; s < 2; ++s)
     for (int i = 0; i < 3; ++i) {
       const D aw = dot3(cof[s] + 3 * i, w);
@@ -422,15 +420,19 @@ __global__ void pair_grad_kernel(long long n_pairs, const PairRec* __restrict__ 
   for (int j = 0; j < 12; ++j) out[j] = g[j];
 }
 
+__global__ void pair_grad_kernel(long long n_pairs, const PairRec* __restrict__ prs,
+                                 const ViewRec* __restrict__ views, const ViewTan* __restrict__ vtan,
+                                 const double* __restrict__ Gpp, double* __restrict__ gpp) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_pairs) return;
+  pair_grad(prs[p], views, vtan, Gpp + 12 * p, gpp + 12 * p);
+}
+
 // Per-view sum of the pair gradients in a fixed order (one block per view):
 // deterministic grad[view][6].  With pairs == NULL the pairs of a view are found
 // by the row-major a < b enumeration, otherwise by scanning the pair list.
-__global__ void __launch_bounds__(256) view_grad_reduce_kernel(int n_views, long long n_pairs,
-                                                               const int32_t* __restrict__ pairs,
-                                                               const double* __restrict__ gpp,
-                                                               double* __restrict__ grad) {
-  __shared__ double sh[6][256];
-  const int lam = blockIdx.x;
+__device__ void view_grad_block(int lam, int n_views, long long n_pairs, const int32_t* __restrict__ pairs,
+                                const double* __restrict__ gpp, double* __restrict__ grad, double (*sh)[256]) {
   double acc[6] = {0, 0, 0, 0, 0, 0};
   if (pairs) {
     for (long long p = threadIdx.x; p < n_pairs; p += blockDim.x) {
@@ -458,9 +460,97 @@ __global__ void __launch_bounds__(256) view_grad_reduce_kernel(int n_views, long
     __syncthreads();
   }
   if (threadIdx.x < 6) grad[6 * lam + threadIdx.x] = sh[threadIdx.x][0];
+  __syncthreads();
 }
 
-// Row directions (cos, sin)(m pi / n_alpha) in FP64 for the anchor look-ups.
+__global__ void __launch_bounds__(256) view_grad_reduce_kernel(int n_views, long long n_pairs,
+                                                               const int32_t* __restrict__ pairs,
+                                                               const double* __restrict__ gpp,
+                                                               double* __restrict__ grad) {
+  __shared__ double sh[6][256];
+  view_grad_block(blockIdx.x, n_views, n_pairs, pairs, gpp, grad, sh);
+}
+
+// ---------------------------------------------------------------- serving rounds
+__global__ void serve_view_kernel(const ServeJob* __restrict__ jobs, const long long* __restrict__ voff, int n_jobs,
+                                  long long total) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int j = serve_job_of(voff, n_jobs, i);
+  const ServeJob& J = jobs[j];
+  const long long v = i - voff[j];
+  const ViewRec r = setup_view(J.P + 12 * v, J.theta + 6 * v, J.W, J.H);
+  if (r.status) atomicOr(J.status, kStatusDegenerateView);
+  J.views[v] = r;
+  if (J.do_grad) J.vtan[v] = view_tangent(J.P + 12 * v, J.theta + 6 * v, J.W, J.H);
+}
+
+__global__ void serve_pair_setup_kernel(const ServeJob* __restrict__ jobs, const long long* __restrict__ poff,
+                                        int n_jobs, long long total) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int j = serve_job_of(poff, n_jobs, i);
+  const ServeJob& J = jobs[j];
+  const long long p = i - poff[j];
+  int a, b;
+  pair_from_index(p, J.n_views, &a, &b);
+  const PairRec r = setup_pair(a, b, J.n_views, J.views, J.W, J.H, J.pair.K,
+                               const_cast<double2*>(J.pair.ctile) + p * J.n_tiles, J.n_tiles, nullptr);
+  if (r.status) atomicOr(J.status, kStatusDegeneratePair);
+  const_cast<PairRec*>(J.pair.prs)[p] = r;
+}
+
+__global__ void serve_pair_grad_kernel(const ServeJob* __restrict__ jobs, const long long* __restrict__ poff,
+                                       int n_jobs, long long total) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int j = serve_job_of(poff, n_jobs, i);
+  const ServeJob& J = jobs[j];
+  if (!J.do_grad) return;
+  const long long p = i - poff[j];
+  pair_grad(J.pair.prs[p], J.views, J.vtan, J.pair.Gpp + 12 * p, J.gpp + 12 * p);
+}
+
+__global__ void __launch_bounds__(256) serve_view_grad_kernel(const ServeJob* __restrict__ jobs,
+                                                              const long long* __restrict__ voff, int n_jobs) {
+  __shared__ double sh[6][256];
+  const long long i = blockIdx.x;
+  const int j = serve_job_of(voff, n_jobs, i);
+  const ServeJob& J = jobs[j];
+  if (!J.do_grad) return;  // block-uniform
+  view_grad_block((int)(i - voff[j]), J.n_views, J.pair.n_pairs, nullptr, J.gpp, J.grad, sh);
+}
+
+__global__ void serve_step_kernel(const ServeJob* __restrict__ jobs, const long long* __restrict__ voff, int n_jobs,
+                                  long long total) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 6 * total) return;
+  const int j = serve_job_of(voff, n_jobs, i / 6);
+  const ServeJob& J = jobs[j];
+  if (!J.do_grad) return;
+  const long long k = i - 6 * voff[j];
+  J.theta[k] = J.theta[k] - J.step * J.grad[k];
+}
+
+cudaError_t launch_serve_setup(const ServeJob* jobs, const long long* voff, const long long* poff, int n_jobs,
+                               long long n_views, long long n_pairs, cudaStream_t stream) {
+  if (n_views > 0) serve_view_kernel<<<(unsigned)((n_views + 63) / 64), 64, 0, stream>>>(jobs, voff, n_jobs, n_views);
+  if (n_pairs > 0)
+    serve_pair_setup_kernel<<<(unsigned)((n_pairs + 127) / 128), 128, 0, stream>>>(jobs, poff, n_jobs, n_pairs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_serve_grad(const ServeJob* jobs, const long long* voff, const long long* poff, int n_jobs,
+                              long long n_views, long long n_pairs, cudaStream_t stream) {
+  if (n_pairs > 0)
+    serve_pair_grad_kernel<<<(unsigned)((n_pairs + 63) / 64), 64, 0, stream>>>(jobs, poff, n_jobs, n_pairs);
+  if (n_views > 0) {
+    serve_view_grad_kernel<<<(unsigned)n_views, 256, 0, stream>>>(jobs, voff, n_jobs);
+    serve_step_kernel<<<(unsigned)((6 * n_views + 255) / 256), 256, 0, stream>>>(jobs, voff, n_jobs, n_views);
+  }
+  return cudaGetLastError();
+}
+
 __global__ void alpha_dir_kernel(int n_alpha, double2* __restrict__ dir) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= n_alpha) return;

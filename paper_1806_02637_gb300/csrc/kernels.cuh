@@ -47,6 +47,24 @@ struct LaunchHooks {
   }
 };
 
+// Parameters of the pair kernel for one scan (device pointers).
+struct PairArgs {
+  long long n_pairs;
+  const PairRec* prs;
+  const double2* ctile;
+  int n_tiles;
+  const double2* alpha_dir;
+  const void* sino;
+  const float* scales;  // FP16 storage only, else NULL
+  int n_alpha, n_s, K;
+  double inv_ds;
+  float cauchy_c;
+  double* per_pair;
+  int32_t* nk_out;
+  double* block_partial;
+  double* Gpp;  // adjoint output, NULL for the plain evaluation
+};
+
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_radon(const ViewRec* views, int n_views, const float* images, int W, int H, int n_alpha, int n_s,
                          int dtype, void* sino_out, float* scales_out, RadonRow* table, void* wimg, float* stage,
@@ -64,5 +82,49 @@ cudaError_t launch_ecc_pairs(long long n_pairs, const PairRec* prs, const double
 
 cudaError_t launch_reduce(const double* partial, int n, double* total, const LaunchHooks& hooks,
                           cudaStream_t stream);
+
+// ---------------------------------------------------------------- serving rounds
+// One active job of a serving round (device copy of the scheduler's table).  Every
+// round evaluates each job's total and, with do_grad, its gradient and one step
+// theta <- theta - step * grad.  The kernels below cover all jobs of a round; a
+// flattened index (view, pair or pair block) is mapped to its job by binary search
+// over the per-job prefix offsets (n_jobs + 1 entries each).
+struct ServeJob {
+  PairArgs pair;  // pair kernel parameters (block_partial and Gpp set, per_pair/nk_out NULL)
+  int dtype;
+  int n_views, W, H, n_tiles;
+  int do_grad;
+  double step;
+  const double* P;   // [n_views][12]
+  double* theta;     // [n_views][6]
+  double* grad;      // [n_views][6]
+  ViewRec* views;
+  ViewTan* vtan;
+  double* gpp;        // [n_pairs][12]
+  double* total_out;  // this round's total
+  int* status;
+};
+
+__host__ __device__ inline int serve_job_of(const long long* off, int n_jobs, long long i) {
+  int lo = 0, hi = n_jobs - 1;  // last job with off[j] <= i
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Per-view set-up and tangents; per-pair set-up.
+cudaError_t launch_serve_setup(const ServeJob* jobs, const long long* voff, const long long* poff, int n_jobs,
+                               long long n_views, long long n_pairs, cudaStream_t stream);
+// Pair kernel over all jobs' pair blocks: a persistent grid that takes blocks from a
+// counter (reset here), then each job's fixed-order total.
+cudaError_t launch_serve_pairs(const ServeJob* jobs, const long long* boff, int n_jobs,
+                               unsigned long long* counter, int grid, cudaStream_t stream);
+int serve_pairs_blocks_per_sm();
+// Pair gradients, per-view gradient sums and the gradient steps.
+cudaError_t launch_serve_grad(const ServeJob* jobs, const long long* voff, const long long* poff, int n_jobs,
+                              long long n_views, long long n_pairs, cudaStream_t stream);
 
 }  // namespace ecc
