@@ -37,7 +37,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x m
 FLOPS_PER_TAP = 4                                    # lerp (sub + fma) + accumulate
 
 
-def parse_args():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -51,7 +51,7 @@ def parse_args():
     ap.add_argument("--serve-rate", type=float, default=20.0, help="mean Poisson arrival rate [jobs/s]")
     ap.add_argument("--views", type=int, default=0,
                     help="use the first N views of the workload (smaller case for profiling); 0 = all")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def measured_peaks():
@@ -278,12 +278,17 @@ def serving_leg(args, c2_scan):
 
 
 # ------------------------------------------------------------------ CPU baseline
-def oracle_sample(cfg, scan, n_views_sample: int, n_threads: int):
+def sample_views(cfg, n_views_sample: int):
+    return np.linspace(0, cfg.n_views - 1, n_views_sample).round().astype(int)
+
+
+def oracle_sample(cfg, scan, n_views_sample: int, n_threads: int, sampled: bool = False):
     """Times the oracle on a bounded sample of the workload: the dRadon/ds of
     n_views_sample views and the ECC of all pairs among them; extrapolates the
-    per-view and per-pair costs to the whole job."""
+    per-view and per-pair costs to the whole job.  `scan` holds either all views
+    or (sampled=True) only the views of sample_views()."""
     from oracle import oracle as orc
-    idx = np.linspace(0, cfg.n_views - 1, n_views_sample).round().astype(int)
+    idx = slice(None) if sampled else sample_views(cfg, n_views_sample)
     P = scan["P"][idx]
     imgs = scan["images"][idx]
     t0 = time.perf_counter()
@@ -304,11 +309,11 @@ def run_reference(args):
     if rank != 0:
         return 0
     cfg = synth.CONFIGS[args.workload]
-    scan = synth.make_scan(cfg)
+    scan = synth.make_scan(cfg, views=sample_views(cfg, 12))
     cores = os.cpu_count() or 1
     vals, infos = [], []
     for it in range(args.warmup + args.steps):
-        v, info = oracle_sample(cfg, scan, 12, cores)
+        v, info = oracle_sample(cfg, scan, 12, cores, sampled=True)
         if it >= args.warmup:
             vals.append(v)
             infos.append(info)
