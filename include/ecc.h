@@ -268,7 +268,7 @@ int ecc_serve_stats(ecc_ctx* ctx, long long* rounds, long long* job_rounds, int*
  * allocate device memory while running (an application that gives all free device
  * memory to its own pool at start-up, or a fixed-budget pipeline that cannot take
  * an allocation's implicit device synchronisation).  Its scratch lives in one
- * 4 MiB statically sized device array inside the library; it calls no allocator.
+ * 5 MiB statically sized device array inside the library; it calls no allocator.
  *
  *   Device: the current CUDA device; all device pointers must be on it.  The first
  *   call on each device resolves the scratch array's address (cudaGetSymbolAddress

@@ -204,8 +204,8 @@ int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion,
   const long long n_blocks = (np + 7) / 8;
   if ((rc = ensure(c, c->views, sizeof(ecc::ViewRec) * (size_t)n_views, "views")) != ECC_OK) return rc;
   if ((rc = ensure(c, c->pairs, sizeof(ecc::PairRec) * (size_t)np, "pairs")) != ECC_OK) return rc;
-  if ((rc = ensure(c, c->ctile, sizeof(double2) * (size_t)np * n_tiles, "tile directions")) != ECC_OK) return rc;
-  if ((rc = ensure(c, c->adir, sizeof(double2) * (size_t)n_alpha, "alpha directions")) != ECC_OK) return rc;
+  if ((rc = ensure(c, c->ctile, sizeof(float4) * (size_t)np * n_tiles, "tile directions")) != ECC_OK) return rc;
+  if ((rc = ensure(c, c->adir, sizeof(float4) * (size_t)n_alpha, "alpha directions")) != ECC_OK) return rc;
   if ((rc = ensure(c, c->partial, sizeof(double) * (size_t)n_blocks, "block partials")) != ECC_OK) return rc;
   if (!per_pair) {
     if ((rc = ensure(c, c->perpair, sizeof(double) * 2 * (size_t)np, "per-pair")) != ECC_OK) return rc;
@@ -224,19 +224,18 @@ int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion,
   hk.on_end("view_setup_kernel", s);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "view set-up launch");
   hk.on_begin("alpha_dir_kernel", s);
-  ecc::alpha_dir_kernel<<<(n_alpha + 255) / 256, 256, 0, s>>>(n_alpha, (double2*)c->adir.p);
+  ecc::alpha_dir_kernel<<<(n_alpha + 255) / 256, 256, 0, s>>>(n_alpha, (float4*)c->adir.p);
   hk.on_end("alpha_dir_kernel", s);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "alpha table launch");
   hk.on_begin("pair_setup_kernel", s);
   ecc::pair_setup_kernel<<<(unsigned)((np + 127) / 128), 128, 0, s>>>(
       n_views, np, pairs, (const ecc::ViewRec*)c->views.p, W, H, n_kappa, (ecc::PairRec*)c->pairs.p,
-      (double2*)c->ctile.p, n_tiles, reuse ? 1 : 0, c->d_status);
+      (float4*)c->ctile.p, n_tiles, reuse ? 1 : 0, c->d_status);
   hk.on_end("pair_setup_kernel", s);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "pair set-up launch");
-  const double inv_ds = (double)(n_s - 1) / std::sqrt((double)W * W + (double)H * H);
   int nb = 0;
-  e = ecc::launch_ecc_pairs(np, (const ecc::PairRec*)c->pairs.p, (const double2*)c->ctile.p, n_tiles,
-                            (const double2*)c->adir.p, sino, scales, dtype, n_alpha, n_s, n_kappa, inv_ds, cauchy_c,
+  e = ecc::launch_ecc_pairs(np, (const ecc::PairRec*)c->pairs.p, (const float4*)c->ctile.p, n_tiles,
+                            (const float4*)c->adir.p, sino, scales, dtype, n_alpha, n_s, n_kappa, W, H, cauchy_c,
                             per_pair, nkappa, (double*)c->partial.p, grad ? (double*)c->Gpp.p : nullptr, &nb, hk,
                             s);
   if (e != cudaSuccess) return cuda_fail(c, e, "pair kernel launch");

@@ -15,6 +15,7 @@
 #include <cuda_fp16.h>
 
 #include "ecc_internal.cuh"
+#include "df.cuh"
 #include "kernels.cuh"
 
 namespace ecc {
@@ -88,28 +89,34 @@ __device__ __forceinline__ Anchor shfl_anchor(const Anchor& x, int src) {
   return r;
 }
 
-// FP64 anchor of one (view, tile): the epipolar line l = A c (centred detector
-// coordinates) of the tile-centre plane, folded to alpha in [0, pi), located on
-// the alpha grid against the exact row direction, and its s offset.
-__device__ Anchor make_anchor(const double* __restrict__ A, double2 c, const double2* __restrict__ alpha_dir,
-                              int n_alpha, float inv_dalpha, double inv_ds, double half_ns1, float inv_ds_f,
-                              double dk) {
-  double l0 = A[0] * c.x + A[1] * c.y;
-  double l1 = A[2] * c.x + A[3] * c.y;
-  double l2 = A[4] * c.x + A[5] * c.y;
+// Anchor of one (view, tile): the epipolar line l = A c (centred detector
+// coordinates) of the tile-centre plane, folded to alpha in [0, pi), located on the
+// alpha grid against the exact row direction, and its s offset.  The construction
+// needs more than FP32 (l is a sum of products of FP64-sized terms, and the s index
+// must hold 1e-7 bins over hundreds of bins), and GB300 issues FP64 at 1/64 of the
+// FP32 rate, so it runs in double-float arithmetic (about 48 bits) on the FP32
+// pipes; A, c and the row directions arrive split into (hi, lo) pairs.
+__device__ Anchor make_anchor(const float* __restrict__ Adf, float4 c, const float4* __restrict__ alpha_dir,
+                              int n_alpha, float inv_dalpha, df inv_ds, df half_ns1, float inv_ds_f, df dk) {
+  const df cx = {c.x, c.z}, cy = {c.y, c.w};
+  const df A0 = {Adf[0], Adf[1]}, A1 = {Adf[2], Adf[3]}, A2 = {Adf[4], Adf[5]};
+  const df A3 = {Adf[6], Adf[7]}, A4 = {Adf[8], Adf[9]}, A5 = {Adf[10], Adf[11]};
+  df l0 = df_add(df_mul(A0, cx), df_mul(A1, cy));
+  df l1 = df_add(df_mul(A2, cx), df_mul(A3, cy));
+  df l2 = df_add(df_mul(A4, cx), df_mul(A5, cy));
   // derivative of the line with respect to kappa: A c_perp, c_perp = (-c.y, c.x)
-  double p0 = A[1] * c.x - A[0] * c.y;
-  double p1 = A[3] * c.x - A[2] * c.y;
-  double p2 = A[5] * c.x - A[4] * c.y;
+  df p0 = df_sub(df_mul(A1, cx), df_mul(A0, cy));
+  df p1 = df_sub(df_mul(A3, cx), df_mul(A2, cy));
+  df p2 = df_sub(df_mul(A5, cx), df_mul(A4, cy));
   Anchor r;
   r.sg = 1.0f;
-  if (l1 < 0.0 || (l1 == 0.0 && l0 < 0.0)) {
-    l0 = -l0; l1 = -l1; l2 = -l2;
-    p0 = -p0; p1 = -p1; p2 = -p2;
+  if (l1.hi < 0.0f || (l1.hi == 0.0f && l0.hi < 0.0f)) {
+    l0 = df_neg(l0); l1 = df_neg(l1); l2 = df_neg(l2);
+    p0 = df_neg(p0); p1 = df_neg(p1); p2 = df_neg(p2);
     r.sg = -1.0f;
   }
-  const float l0f = (float)l0, l1f = (float)l1;
-  const float q0 = (float)p0, q1 = (float)p1, q2 = (float)p2;
+  const float l0f = l0.hi, l1f = l1.hi;
+  const float q0 = p0.hi, q1 = p1.hi, q2 = p2.hi;
   const float h = sqrtf(l0f * l0f + l1f * l1f);
   const float ih_f = 1.0f / h;
   const float chx = l0f * ih_f, chy = l1f * ih_f;
@@ -118,35 +125,30 @@ __device__ Anchor make_anchor(const double* __restrict__ A, double2 c, const dou
   r.p3 = q2 * ih_f;
   int m = (int)floorf(atan2f(l1f, l0f) * inv_dalpha);
   m = m < 0 ? 0 : (m > n_alpha - 1 ? n_alpha - 1 : m);
-  const double2 u = alpha_dir[m];
-  const double cr = u.x * l1 - u.y * l0;   // h sin(alpha - alpha_m), no cancellation loss in FP64
-  const double dt = u.x * l0 + u.y * l1;   // h cos(alpha - alpha_m)
-  const float th = atan2f((float)cr, (float)dt);
+  const float4 u = alpha_dir[m];
+  const df ux = {u.x, u.z}, uy = {u.y, u.w};
+  const df cr = df_sub(df_mul(ux, l1), df_mul(uy, l0));  // h sin(alpha - alpha_m)
+  const df dt = df_add(df_mul(ux, l0), df_mul(uy, l1));  // h cos(alpha - alpha_m)
+  const float th = atan2f(cr.hi, dt.hi);
   r.m0 = m;
   r.fa0 = th * inv_dalpha;
-  // s = -l2 / h = (-l2 / dt) cos(th): FP64 reciprocal from an FP32 seed and one Newton step
-  double rr = (double)(1.0f / (float)dt);
-  rr = fma(rr, fma(-dt, rr, 1.0), rr);
-  const double sigma = -l2 * rr;
-  const double is = fma(sigma, inv_ds, half_ns1);
-  const double nf = floor(is);
+  // s = -l2 / h = (-l2 / dt) cos(th)
+  const df sigma = df_neg(df_mul(l2, df_recip(dt)));
+  float frac;
+  const float nf = df_floor_frac(df_add(df_mul(sigma, inv_ds), half_ns1), &frac);
   const float sh = sinf(0.5f * th);
-  const float sigf = (float)sigma;
+  const float sigf = sigma.hi;
   r.n0 = (int)nf;
-  r.fs0 = (float)(is - nf) - sigf * 2.0f * sh * sh * inv_ds_f;
+  r.fs0 = frac - sigf * 2.0f * sh * sh * inv_ds_f;
   r.s0 = sigf * cosf(th);
-  // exact first-order advance of the s index per sample: (ds/dkappa) dk / ds_bin in
-  // FP64, ds/dkappa = (1/h) (-l2' + l2 (l . l') / h^2); 1/h from an FP32 reciprocal
-  // square-root seed and one FP64 Newton step (relative error ~1e-13; th may reach a
-  // whole alpha row spacing, so no series in th is used here)
-  const double h2 = fma(l0, l0, l1 * l1);
-  double ihd = (double)rsqrtf((float)h2);
-  ihd = ihd * fma(-0.5 * h2, ihd * ihd, 1.5);
-  const double t1 = l0 * p0 + l1 * p1;
-  const double g = ihd * (-p2 + l2 * t1 * ihd * ihd) * dk * inv_ds;
-  const float gh = __int_as_float(__float_as_int((float)g) & (int)0xffffffc0);
+  // exact first-order advance of the s index per sample: (ds/dkappa) dk / ds_bin,
+  // ds/dkappa = (1/h) (-l2' + l2 (l . l') / h^2)
+  const df ih = df_rsqrt(df_add(df_mul(l0, l0), df_mul(l1, l1)));
+  const df t1 = df_add(df_mul(l0, p0), df_mul(l1, p1));
+  const df g = df_mul(df_mul(df_mul(ih, df_sub(df_mul(df_mul(l2, t1), df_mul(ih, ih)), p2)), dk), inv_ds);
+  const float gh = __int_as_float(__float_as_int(g.hi) & (int)0xffffffc0);
   r.gh = gh;
-  r.gl = (float)(g - (double)gh);
+  r.gl = (g.hi - gh) + g.lo;
   return r;
 }
 
@@ -265,17 +267,19 @@ __device__ __forceinline__ float sample_grad(const T* __restrict__ sv, int n_alp
 }
 
 // One pair per warp (one plane per lane, tiles of 32): d, e and N_kappa of pair p
-// and, for GRAD, the adjoint d e / d A; returns e on every lane.
+// and, for GRAD, the adjoint d e / d A; returns e on every lane.  Inlined into the
+// single-scan kernel and the serving kernel; the two compiled copies may round
+// FP32 operations differently (1e-7 relative, well inside the FP32 bar), while
+// each kernel is deterministic.
 template <typename T, bool GRAD>
 __device__ __forceinline__ double pair_warp(const PairArgs& g, long long p, int lane) {
   const PairRec* __restrict__ prs = g.prs;
-  const double2* __restrict__ ctile = g.ctile;
+  const float4* __restrict__ ctile = g.ctile;
   const int n_tiles = g.n_tiles;
-  const double2* __restrict__ alpha_dir = g.alpha_dir;
+  const float4* __restrict__ alpha_dir = g.alpha_dir;
   const T* __restrict__ sino = static_cast<const T*>(g.sino);
   const float* __restrict__ scales = g.scales;
   const int n_alpha = g.n_alpha, n_s = g.n_s, K = g.K;
-  const double inv_ds = g.inv_ds;
   const float cauchy_c = g.cauchy_c;
   double* __restrict__ per_pair = g.per_pair;
   int32_t* __restrict__ nk_out = g.nk_out;
@@ -295,12 +299,14 @@ __device__ __forceinline__ double pair_warp(const PairArgs& g, long long p, int 
       const T* sb = sino + (size_t)pr.b * vstride;
       const float sca = scales ? scales[pr.a] : 1.0f;
       const float scb = scales ? scales[pr.b] : 1.0f;
-      const float inv_dalpha = (float)((double)n_alpha / kPi);
-      const double half_ns1 = 0.5 * (n_s - 1);
-      const float inv_ds_f = (float)inv_ds;
+      const float inv_dalpha = g.inv_dalpha;
+      const df inv_ds = {g.inv_ds_hi, g.inv_ds_lo};
+      const df half_ns1 = {g.half_hi, g.half_lo};
+      const float inv_ds_f = g.inv_ds_f;
       // offset of this lane's plane from its tile centre: (j + 1/2 - n_t/2) dk for a
       // tile of n_t samples (n_t = 32 except for the last tile)
-      const float dkf = (float)pr.dk;
+      const float dkf = pr.dk_hi;
+      const df dk = {pr.dk_hi, pr.dk_lo};
       const float jj_full = (float)lane - 15.5f;
       const float jj_last = (float)lane + 0.5f - 0.5f * (float)(K - 32 * (n_tiles - 1));
       const float de_full = jj_full * dkf, de_last = jj_last * dkf;
@@ -308,11 +314,11 @@ __device__ __forceinline__ double pair_warp(const PairArgs& g, long long p, int 
       sincosf(de_full, &sd, &cd);
       sincosf(de_last, &sd_last, &cd_last);
       const int r0lo = pr.r0lo, r0hi = pr.r0hi, r1lo = pr.r1lo, r1hi = pr.r1hi;
-      const double2* ct = ctile + p * n_tiles;
+      const float4* ct = ctile + p * n_tiles;
       float Af[12];
       if (GRAD) {
 #pragma unroll
-        for (int i = 0; i < 12; ++i) Af[i] = (float)(&pr.A[0][0])[i];
+        for (int i = 0; i < 12; ++i) Af[i] = (&pr.Af[0][0])[2 * i];
       }
       for (int t0 = 0; t0 < n_tiles; t0 += 16) {
         Anchor mine;
@@ -320,7 +326,7 @@ __device__ __forceinline__ double pair_warp(const PairArgs& g, long long p, int 
           const int v = lane >> 4;
           int t = t0 + (lane & 15);
           if (t >= n_tiles) t = n_tiles - 1;
-          mine = make_anchor(pr.A[v], ct[t], alpha_dir, n_alpha, inv_dalpha, inv_ds, half_ns1, inv_ds_f, pr.dk);
+          mine = make_anchor(pr.Af[v], ct[t], alpha_dir, n_alpha, inv_dalpha, inv_ds, half_ns1, inv_ds_f, dk);
         }
         const int tmax = min(16, n_tiles - t0);
         for (int tt = 0; tt < tmax; ++tt) {
@@ -338,8 +344,8 @@ __device__ __forceinline__ double pair_warp(const PairArgs& g, long long p, int 
             acc += valid ? dd * dd : 0.0f;
           } else {
             // this lane's plane direction c_k in the (w, v) frame
-            const double2 ctd = ct[t0 + tt];
-            const float cx = (float)ctd.x, cy = (float)ctd.y;
+            const float4 ctd = ct[t0 + tt];
+            const float cx = ctd.x, cy = ctd.y;
             const float ckx = cx * c_ - cy * s_, cky = cx * s_ + cy * c_;
             float ga[3], gb[3];
             const float Sa = sample_grad(sa, n_alpha, n_s, aa, c_, s_, jj, de, inv_dalpha, inv_ds_f,
@@ -476,9 +482,9 @@ __global__ void __launch_bounds__(1024) serve_reduce_kernel(const ServeJob* __re
 
 }  // namespace
 
-cudaError_t launch_ecc_pairs(long long n_pairs, const PairRec* prs, const double2* ctile, int n_tiles,
-                             const double2* alpha_dir, const void* sino, const float* scales, int dtype,
-                             int n_alpha, int n_s, int K, double inv_ds, double cauchy_c, double* per_pair,
+cudaError_t launch_ecc_pairs(long long n_pairs, const PairRec* prs, const float4* ctile, int n_tiles,
+                             const float4* alpha_dir, const void* sino, const float* scales, int dtype,
+                             int n_alpha, int n_s, int K, int W, int H, double cauchy_c, double* per_pair,
                              int32_t* nk_out, double* block_partial, double* Gpp, int* n_blocks_out,
                              const LaunchHooks& hooks, cudaStream_t stream) {
   const long long nb = (n_pairs + kWarpsPerBlock - 1) / kWarpsPerBlock;
@@ -496,10 +502,8 @@ cudaError_t launch_ecc_pairs(long long n_pairs, const PairRec* prs, const double
   g.alpha_dir = alpha_dir;
   g.sino = sino;
   g.scales = dtype == 1 ? scales : nullptr;
-  g.n_alpha = n_alpha;
-  g.n_s = n_s;
+  pair_args_grid(g, n_alpha, n_s, W, H);
   g.K = K;
-  g.inv_ds = inv_ds;
   g.cauchy_c = cc;
   g.per_pair = per_pair;
   g.nk_out = nk_out;

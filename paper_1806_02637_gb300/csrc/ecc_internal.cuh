@@ -37,6 +37,8 @@ struct ViewTan {
 // Per-pair set-up (FP64 geometry, integer sample ranges).
 struct PairRec {
   double A[2][6];   // per view (a, b): l_centred(kappa) = A (cos kappa, sin kappa), 3x2 row-major
+  float Af[2][12];  // A as double-float pairs (hi, lo) per entry, for the pair kernel's anchors
+  float dk_hi, dk_lo;  // Delta kappa as a double-float pair
   double c0[2];     // direction of the first sample, (k + 1/2) = 1/2, in the (w, v) frame
   double rot[2];    // cos, sin of one sample step Delta kappa
   double dk;        // Delta kappa
@@ -51,6 +53,13 @@ enum : int {
   kStatusDegenerateView = 1,
   kStatusDegeneratePair = 2,
 };
+
+// A unit direction (x, y) split into double-float pairs: (hi.x, hi.y, lo.x, lo.y).
+// Layout of the tile-centre directions and of the alpha-row directions.
+__host__ __device__ inline float4 split_dir(double x, double y) {
+  const float hx = (float)x, hy = (float)y;
+  return make_float4(hx, hy, (float)(x - (double)hx), (float)(y - (double)hy));
+}
 
 __host__ __device__ inline void pair_from_index(long long p, int n_views, int* a, int* b) {
   // row-major upper-triangular enumeration of a < b

@@ -27,11 +27,11 @@
 
 // The scratch array itself.  Its device address is only ever obtained through
 // cudaGetSymbolAddress below; host code never uses the symbol as a pointer.
-static __device__ __align__(256) unsigned char g_noalloc_scratch[size_t(4) << 20];
+static __device__ __align__(256) unsigned char g_noalloc_scratch[size_t(5) << 20];
 
 namespace {
 
-// Limits of the static scratch (4 MiB).
+// Limits of the static scratch (5 MiB).
 constexpr int kMaxViews = 512;
 constexpr int kMaxAlpha = 4096;
 constexpr int kMaxPairs = 8192;
@@ -44,11 +44,11 @@ constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 constexpr size_t kOffStatus = 0;
 constexpr size_t kOffViews = align256(kOffStatus + sizeof(int));
 constexpr size_t kOffAlpha = align256(kOffViews + sizeof(ecc::ViewRec) * kMaxViews);
-constexpr size_t kOffPairs = align256(kOffAlpha + sizeof(double2) * kMaxAlpha);
+constexpr size_t kOffPairs = align256(kOffAlpha + sizeof(float4) * kMaxAlpha);
 constexpr size_t kOffPartial = align256(kOffPairs + sizeof(ecc::PairRec) * kMaxPairs);
 constexpr size_t kOffPerPair = align256(kOffPartial + sizeof(double) * ((kMaxPairs + 7) / 8));
 constexpr size_t kOffTiles = align256(kOffPerPair + sizeof(double) * 2 * kMaxPairs);
-constexpr size_t kEnd = kOffTiles + sizeof(double2) * kMaxPairTiles;
+constexpr size_t kEnd = kOffTiles + sizeof(float4) * kMaxPairTiles;
 static_assert(kEnd <= kScratchBytes, "no-alloc scratch layout exceeds the static array");
 
 // Device address of the array, resolved once per device with that device current.
@@ -117,10 +117,10 @@ extern "C" int ecc_evaluate_noalloc(int n_views, const double* P, const double* 
   cudaStream_t s = (cudaStream_t)stream;
   int* status = reinterpret_cast<int*>(base + kOffStatus);
   ecc::ViewRec* views = reinterpret_cast<ecc::ViewRec*>(base + kOffViews);
-  double2* adir = reinterpret_cast<double2*>(base + kOffAlpha);
+  float4* adir = reinterpret_cast<float4*>(base + kOffAlpha);
   ecc::PairRec* prs = reinterpret_cast<ecc::PairRec*>(base + kOffPairs);
   double* partial = reinterpret_cast<double*>(base + kOffPartial);
-  double2* ctile = reinterpret_cast<double2*>(base + kOffTiles);
+  float4* ctile = reinterpret_cast<float4*>(base + kOffTiles);
   if (!per_pair) per_pair = reinterpret_cast<double*>(base + kOffPerPair);
 
   if (n_pairs == 0) {
@@ -136,9 +136,8 @@ extern "C" int ecc_evaluate_noalloc(int n_views, const double* P, const double* 
   ecc::pair_setup_kernel<<<(n_pairs + 127) / 128, 128, 0, s>>>(n_views, n_pairs, pairs, views, W, H, n_kappa, prs,
                                                                ctile, n_tiles, 0, status);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail(ECC_ECUDA, cudaGetErrorString(e));
-  const double inv_ds = (double)(n_s - 1) / std::sqrt((double)W * W + (double)H * H);
   int nb = 0;
-  e = ecc::launch_ecc_pairs(n_pairs, prs, ctile, n_tiles, adir, sino, scales, dtype, n_alpha, n_s, n_kappa, inv_ds,
+  e = ecc::launch_ecc_pairs(n_pairs, prs, ctile, n_tiles, adir, sino, scales, dtype, n_alpha, n_s, n_kappa, W, H,
                             cauchy_c, per_pair, nkappa, partial, nullptr, &nb, hk, s);
   if (e != cudaSuccess) return fail(ECC_ECUDA, cudaGetErrorString(e));
   e = ecc::launch_reduce(partial, nb, total, hk, s);

@@ -240,7 +240,7 @@ __host__ __device__ double view_arc(const double* A, int W, int H, double* clo) 
 // n_tiles entries).  With previous != NULL the sampling of *previous is kept and
 // only the maps follow the geometry.
 __host__ __device__ PairRec setup_pair(int a, int b, int n_views, const ViewRec* views, int W, int H, int K,
-                                       double2* ctile, int n_tiles, const PairRec* previous) {
+                                       float4* ctile, int n_tiles, const PairRec* previous) {
   const bool reuse_sampling = previous != nullptr;
   PairRec r;
   const bool in_range = a >= 0 && b >= 0 && a < n_views && b < n_views;
@@ -254,6 +254,8 @@ __host__ __device__ PairRec setup_pair(int a, int b, int n_views, const ViewRec*
   r.r0lo = r.r0hi = r.r1lo = r.r1hi = 0;
   r.nk = 0;
   r.dk = 0.0;
+  r.dk_hi = r.dk_lo = 0.0f;
+  for (int i = 0; i < 24; ++i) (&r.Af[0][0])[i] = 0.0f;
   r.c0[0] = 1.0;
   r.c0[1] = 0.0;
   r.rot[0] = 1.0;
@@ -337,14 +339,14 @@ __host__ __device__ PairRec setup_pair(int a, int b, int n_views, const ViewRec*
     sincos(32.0 * dk, &s32, &c32);
     double cx0 = c16 * csx - s16 * csy;
     double cy0 = s16 * csx + c16 * csy;
-    double2* ct = ctile;
+    float4* ct = ctile;
     for (int t = 0; t < n_tiles; ++t) {
       if (32 * t + 32 <= K) {
-        ct[t] = make_double2(cx0, cy0);
+        ct[t] = split_dir(cx0, cy0);
       } else {  // last, partial tile
         double sp, cp;
         sincos(0.5 * (32.0 * t + K) * dk, &sp, &cp);
-        ct[t] = make_double2(cp * csx - sp * csy, sp * csx + cp * csy);
+        ct[t] = split_dir(cp * csx - sp * csy, sp * csx + cp * csy);
       }
       const double nx = c32 * cx0 - s32 * cy0;
       const double ny = s32 * cx0 + c32 * cy0;
@@ -353,12 +355,21 @@ __host__ __device__ PairRec setup_pair(int a, int b, int n_views, const ViewRec*
     }
   }
   if (!ok) r.status = 1;
+  // double-float copies for the pair kernel
+  for (int s = 0; s < 2; ++s)
+    for (int i = 0; i < 6; ++i) {
+      const float h = (float)r.A[s][i];
+      r.Af[s][2 * i] = h;
+      r.Af[s][2 * i + 1] = (float)(r.A[s][i] - (double)h);
+    }
+  r.dk_hi = (float)r.dk;
+  r.dk_lo = (float)(r.dk - (double)r.dk_hi);
   return r;
 }
 
 __global__ void pair_setup_kernel(int n_views, long long n_pairs, const int32_t* __restrict__ pairs,
                                   const ViewRec* __restrict__ views, int W, int H, int K,
-                                  PairRec* __restrict__ out, double2* __restrict__ ctile, int n_tiles,
+                                  PairRec* __restrict__ out, float4* __restrict__ ctile, int n_tiles,
                                   int reuse_sampling, int* __restrict__ status) {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n_pairs) return;
@@ -495,7 +506,7 @@ __global__ void serve_pair_setup_kernel(const ServeJob* __restrict__ jobs, const
   int a, b;
   pair_from_index(p, J.n_views, &a, &b);
   const PairRec r = setup_pair(a, b, J.n_views, J.views, J.W, J.H, J.pair.K,
-                               const_cast<double2*>(J.pair.ctile) + p * J.n_tiles, J.n_tiles, nullptr);
+                               const_cast<float4*>(J.pair.ctile) + p * J.n_tiles, J.n_tiles, nullptr);
   if (r.status) atomicOr(J.status, kStatusDegeneratePair);
   const_cast<PairRec*>(J.pair.prs)[p] = r;
 }
@@ -551,12 +562,12 @@ cudaError_t launch_serve_grad(const ServeJob* jobs, const long long* voff, const
   return cudaGetLastError();
 }
 
-__global__ void alpha_dir_kernel(int n_alpha, double2* __restrict__ dir) {
+__global__ void alpha_dir_kernel(int n_alpha, float4* __restrict__ dir) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= n_alpha) return;
   double s, c;
   sincospi((double)m / (double)n_alpha, &s, &c);
-  dir[m] = make_double2(c, s);
+  dir[m] = split_dir(c, s);
 }
 
 }  // namespace ecc
@@ -575,7 +586,7 @@ extern "C" int ecc_internal_setup_pair_host(int n_views, const double* P, const 
   views[0] = ecc::setup_view(P + 12 * a, motion ? motion + 6 * a : nullptr, W, H);
   views[1] = ecc::setup_view(P + 12 * b, motion ? motion + 6 * b : nullptr, W, H);
   const int n_tiles = (K + 31) / 32;
-  double2* ct = new double2[n_tiles];
+  float4* ct = new float4[n_tiles];
   const ecc::PairRec r = ecc::setup_pair(0, 1, 2, views, W, H, K, ct, n_tiles, nullptr);
   delete[] ct;
   info_out[0] = r.c0[0];

@@ -1,5 +1,6 @@
 // Kernel declarations shared by the translation units of the library.
 #pragma once
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 #include "ecc_internal.cuh"
@@ -9,14 +10,14 @@ namespace ecc {
 __global__ void view_setup_kernel(int n_views, const double* P, const double* motion, int W, int H, ViewRec* out,
                                   int* status);
 __global__ void pair_setup_kernel(int n_views, long long n_pairs, const int32_t* pairs, const ViewRec* views, int W,
-                                  int H, int K, PairRec* out, double2* ctile, int n_tiles, int reuse_sampling,
+                                  int H, int K, PairRec* out, float4* ctile, int n_tiles, int reuse_sampling,
                                   int* status);
 __global__ void view_tangent_kernel(int n_views, const double* P, const double* motion, int W, int H, ViewTan* out);
 __global__ void pair_grad_kernel(long long n_pairs, const PairRec* prs, const ViewRec* views, const ViewTan* vtan,
                                  const double* Gpp, double* gpp);
 __global__ void view_grad_reduce_kernel(int n_views, long long n_pairs, const int32_t* pairs, const double* gpp,
                                         double* grad);
-__global__ void alpha_dir_kernel(int n_alpha, double2* dir);
+__global__ void alpha_dir_kernel(int n_alpha, float4* dir);
 
 // Per (view, alpha-row) line parameters of the Joseph line sums (32.32 fixed point).
 struct RadonRow {
@@ -51,19 +52,35 @@ struct LaunchHooks {
 struct PairArgs {
   long long n_pairs;
   const PairRec* prs;
-  const double2* ctile;
+  const float4* ctile;      // tile-centre directions (hi.x, hi.y, lo.x, lo.y)
   int n_tiles;
-  const double2* alpha_dir;
+  const float4* alpha_dir;  // alpha-row directions (cos, sin as double-float pairs)
   const void* sino;
   const float* scales;  // FP16 storage only, else NULL
   int n_alpha, n_s, K;
-  double inv_ds;
+  // grid constants (set by pair_args_grid): alpha rows per radian, s bins per pixel
+  // (FP32 and as a double-float pair), and (n_s - 1) / 2 as a double-float pair
+  float inv_dalpha, inv_ds_f, inv_ds_hi, inv_ds_lo, half_hi, half_lo;
   float cauchy_c;
   double* per_pair;
   int32_t* nk_out;
   double* block_partial;
   double* Gpp;  // adjoint output, NULL for the plain evaluation
 };
+
+inline void pair_args_grid(PairArgs& g, int n_alpha, int n_s, int W, int H) {
+  const double inv_ds = (double)(n_s - 1) / std::sqrt((double)W * W + (double)H * H);
+  const double inv_dalpha = (double)n_alpha / 3.14159265358979323846;
+  const double half = 0.5 * (n_s - 1);
+  g.n_alpha = n_alpha;
+  g.n_s = n_s;
+  g.inv_dalpha = (float)inv_dalpha;
+  g.inv_ds_f = (float)inv_ds;
+  g.inv_ds_hi = (float)inv_ds;
+  g.inv_ds_lo = (float)(inv_ds - (double)g.inv_ds_hi);
+  g.half_hi = (float)half;
+  g.half_lo = (float)(half - (double)g.half_hi);
+}
 
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_radon(const ViewRec* views, int n_views, const float* images, int W, int H, int n_alpha, int n_s,
@@ -74,9 +91,9 @@ int radon_pad(int W, int H, int n_s);
 // Bytes of one view's weighted-image planes (interpolation pairs, both orientations).
 size_t radon_plane_bytes(int W, int H, int n_s);
 
-cudaError_t launch_ecc_pairs(long long n_pairs, const PairRec* prs, const double2* ctile, int n_tiles,
-                             const double2* alpha_dir, const void* sino, const float* scales, int dtype,
-                             int n_alpha, int n_s, int K, double inv_ds, double cauchy_c, double* per_pair, int32_t* nk_out,
+cudaError_t launch_ecc_pairs(long long n_pairs, const PairRec* prs, const float4* ctile, int n_tiles,
+                             const float4* alpha_dir, const void* sino, const float* scales, int dtype,
+                             int n_alpha, int n_s, int K, int W, int H, double cauchy_c, double* per_pair, int32_t* nk_out,
                              double* block_partial, double* Gpp, int* n_blocks_out, const LaunchHooks& hooks,
                              cudaStream_t stream);
 

@@ -73,11 +73,11 @@ Layout layout_of(const ecc_job& j) {
   L.grad = take(n * 6 * sizeof(double));
   L.views = take(n * sizeof(ecc::ViewRec));
   L.vtan = take(n * sizeof(ecc::ViewTan));
-  L.adir = take((size_t)j.n_alpha * sizeof(double2));
+  L.adir = take((size_t)j.n_alpha * sizeof(float4));
   L.sino = take(n * (size_t)j.n_alpha * j.n_s * elem_size(j.dtype));
   L.scales = take(n * sizeof(float));
   L.prs = take(np * sizeof(ecc::PairRec));
-  L.ctile = take(np * n_tiles * sizeof(double2));
+  L.ctile = take(np * n_tiles * sizeof(float4));
   L.partial = take((np + kWarpsPerPairBlock - 1) / kWarpsPerPairBlock * sizeof(double));
   L.Gpp = take(np * 12 * sizeof(double));
   L.gpp = take(np * 12 * sizeof(double));
@@ -189,7 +189,7 @@ bool admit_job(ecc_serve* S, Job* J) {
   }
   ecc::view_setup_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(
       (int)n, (const double*)(R + L.P), nullptr, d.W, d.H, (ecc::ViewRec*)(R + L.views), (int*)(R + L.status));
-  ecc::alpha_dir_kernel<<<(d.n_alpha + 255) / 256, 256, 0, s>>>(d.n_alpha, (double2*)(R + L.adir));
+  ecc::alpha_dir_kernel<<<(d.n_alpha + 255) / 256, 256, 0, s>>>(d.n_alpha, (float4*)(R + L.adir));
   e = cudaGetLastError();
   if (e == cudaSuccess) {
     const ecc::LaunchHooks hk;
@@ -357,15 +357,13 @@ void round_loop(ecc_serve* S) {
       ecc::ServeJob& s = H[i];
       s.pair.n_pairs = np;
       s.pair.prs = (const ecc::PairRec*)(R + L.prs);
-      s.pair.ctile = (const double2*)(R + L.ctile);
+      s.pair.ctile = (const float4*)(R + L.ctile);
       s.pair.n_tiles = (d.n_kappa + 31) / 32;
-      s.pair.alpha_dir = (const double2*)(R + L.adir);
+      s.pair.alpha_dir = (const float4*)(R + L.adir);
       s.pair.sino = R + L.sino;
       s.pair.scales = d.dtype == ECC_F16 ? (const float*)(R + L.scales) : nullptr;
-      s.pair.n_alpha = d.n_alpha;
-      s.pair.n_s = d.n_s;
+      ecc::pair_args_grid(s.pair, d.n_alpha, d.n_s, d.W, d.H);
       s.pair.K = d.n_kappa;
-      s.pair.inv_ds = (double)(d.n_s - 1) / std::sqrt((double)d.W * d.W + (double)d.H * d.H);
       s.pair.cauchy_c = (float)d.cauchy_c;
       s.pair.per_pair = nullptr;
       s.pair.nk_out = nullptr;
