@@ -476,7 +476,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(cfg),
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
             "kernels": kern, "ecc_eval_only": eval_only, "serving": serving, "total": result_total,
-            "geometry_precision": "f64 set-up and anchors, f32 per-sample"}
+            "geometry_precision": "f64 per-view/per-pair set-up, double-float (~48-bit) tile anchors, f32 per-sample"}
     print(json.dumps(line), flush=True)
     return 0
 
