@@ -64,29 +64,41 @@ __device__ __forceinline__ float bilinear(const T* __restrict__ sv, int n_alpha,
   return fmaf(fa, v1 - v0, v0);
 }
 
+constexpr int kSer = 10;           // terms of the per-tile series
+constexpr float kSerLimit = 0.1f;  // series used while |zeta| tan(15.5 dk) <= this
+
+// Per (tile, view) anchor record, 32 floats (128 B), written by one lane and read by
+// the whole warp through shared memory.
 struct Anchor {
   int m0, n0;      // alpha row and s bin of the tile-centre line
   float fa0, fs0;  // fractional parts (may leave [0,1) slightly)
-  float a, b;      // rate of the normal direction in the anchor frame
+  float a, b;      // zeta = a + i b: rate of the normal direction in the anchor frame
   float p3, s0;    // rate of the offset, anchor offset s [px]
   float sg;        // orientation fold of the anchor (+1 / -1)
   float gh, gl;    // exact s-index advance per sample step: gh (17 significant bits) + gl
+  float ser;       // 1: the series below holds over this tile, 0: closed form per sample
+  float dco[kSer];  // alpha offset [bins] = sum_k dco[k-1] t^k,  t = tan(delta)
+  float sco[kSer];  // s remainder [bins] = sco[0] (t - delta) + sum_{k>=2} sco[k-1] t^k
+};
+static_assert(sizeof(Anchor) == 128, "anchor record is 32 floats");
+
+union AnchorVec {
+  Anchor a;
+  float4 v[8];
 };
 
-__device__ __forceinline__ Anchor shfl_anchor(const Anchor& x, int src) {
-  Anchor r;
-  r.m0 = __shfl_sync(0xffffffffu, x.m0, src);
-  r.n0 = __shfl_sync(0xffffffffu, x.n0, src);
-  r.fa0 = __shfl_sync(0xffffffffu, x.fa0, src);
-  r.fs0 = __shfl_sync(0xffffffffu, x.fs0, src);
-  r.a = __shfl_sync(0xffffffffu, x.a, src);
-  r.b = __shfl_sync(0xffffffffu, x.b, src);
-  r.p3 = __shfl_sync(0xffffffffu, x.p3, src);
-  r.s0 = __shfl_sync(0xffffffffu, x.s0, src);
-  r.sg = __shfl_sync(0xffffffffu, x.sg, src);
-  r.gh = __shfl_sync(0xffffffffu, x.gh, src);
-  r.gl = __shfl_sync(0xffffffffu, x.gl, src);
-  return r;
+__device__ __forceinline__ void store_anchor(float4* __restrict__ dst, const Anchor& x) {
+  AnchorVec u;
+  u.a = x;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) dst[i] = u.v[i];
+}
+
+__device__ __forceinline__ Anchor load_anchor(const float4* __restrict__ src) {
+  AnchorVec u;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) u.v[i] = src[i];
+  return u.a;
 }
 
 // Anchor of one (view, tile): the epipolar line l = A c (centred detector
@@ -97,7 +109,8 @@ __device__ __forceinline__ Anchor shfl_anchor(const Anchor& x, int src) {
 // FP32 rate, so it runs in double-float arithmetic (about 48 bits) on the FP32
 // pipes; A, c and the row directions arrive split into (hi, lo) pairs.
 __device__ Anchor make_anchor(const float* __restrict__ Adf, float4 c, const float4* __restrict__ alpha_dir,
-                              int n_alpha, float inv_dalpha, df inv_ds, df half_ns1, float inv_ds_f, df dk) {
+                              int n_alpha, float inv_dalpha, df inv_ds, df half_ns1, float inv_ds_f, df dk,
+                              float tan_half_tile) {
   const df cx = {c.x, c.z}, cy = {c.y, c.w};
   const df A0 = {Adf[0], Adf[1]}, A1 = {Adf[2], Adf[3]}, A2 = {Adf[4], Adf[5]};
   const df A3 = {Adf[6], Adf[7]}, A4 = {Adf[8], Adf[9]}, A5 = {Adf[10], Adf[11]};
@@ -149,23 +162,71 @@ __device__ Anchor make_anchor(const float* __restrict__ Adf, float4 c, const flo
   const float gh = __int_as_float(__float_as_int(g.hi) & (int)0xffffffc0);
   r.gh = gh;
   r.gl = (g.hi - gh) + g.lo;
+  // Series over the tile in t = tan(delta).  In the anchor frame the normal of the
+  // line at delta is cos(delta) (1 + zeta t), zeta = a + i b, so the alpha offset is
+  // arg(1 + zeta t) = sum_k (-1)^(k+1) Im(zeta^k) t^k / k, and
+  //   s(t) = (s0 - p3 t) / |1 + zeta t| = (s0 - p3 t) sum_k e_k t^k,
+  // where (1 + 2 a t + |zeta|^2 t^2)^(-1/2) = sum_k e_k t^k is the Legendre generating
+  // function: e_0 = 1, e_1 = -a, (k + 1) e_(k+1) = -((2k + 1) a e_k + k |zeta|^2 e_(k-1)).
+  // With |zeta t| <= 0.1 the truncation after t^10 is below 1e-10 of the offsets.
+  const float zr = r.a, zi = r.b;
+  const float z2 = fmaf(zr, zr, zi * zi);
+  r.ser = sqrtf(z2) * tan_half_tile <= kSerLimit ? 1.0f : 0.0f;
+  float pre = zr, pim = zi;        // zeta^k
+  float e_prev = 1.0f, e_cur = -zr;  // e_(k-1), e_k
+#pragma unroll
+  for (int k = 1; k <= kSer; ++k) {
+    r.dco[k - 1] = ((k & 1) ? pim : -pim) * inv_dalpha * (1.0f / (float)k);
+    r.sco[k - 1] = fmaf(r.s0, e_cur, -r.p3 * e_prev) * inv_ds_f;
+    const float e_next = -fmaf((float)(2 * k + 1) * zr, e_cur, (float)k * z2 * e_prev) * (1.0f / (float)(k + 1));
+    e_prev = e_cur;
+    e_cur = e_next;
+    const float np = fmaf(pre, zr, -pim * zi), ni = fmaf(pre, zi, pim * zr);
+    pre = np;
+    pim = ni;
+  }
   return r;
 }
 
 // Position of one sample of one view in the sinogram grid, moving from the tile
-// anchor by delta = jj dk (jj a half-integer lane offset; sd, cd = sin, cos delta).
-// alpha: the normal turns by atan2(b sd, cd + a sd) in the anchor frame.  s: the
-// first-order part jj * (gh + gl) is exact (gh * jj is exact in FP32, its integer
-// part split off exactly), and the remainder, of second order in delta, is
-// evaluated in a cancellation-free form:
-//   ds - G1 delta = -(s0 q + p3) u - s0 (q - a) delta,
-//   u = sd/r - delta = ((sin delta - delta) - delta (r - 1)) / r,
-//   r^2 - 1 = sd (2 a cd + (a^2 + b^2 - 1) sd),  q = (2 a cd + (a^2 + b^2) sd)/(cd + r).
+// anchor by delta = jj dk (jj a half-integer lane offset).  The s index splits into
+// the exact first-order part jj * (gh + gl) (gh * jj is exact in FP32, its integer
+// part split off exactly) and a remainder of second order in delta; the alpha
+// index is the anchor's plus the turn of the normal.  Two evaluations:
+//   series (locate_series): both from the anchor's series in t = tan(delta);
+//   closed form (locate): the turn atan2(b sd, cd + a sd) and the remainder in a
+//   cancellation-free form,
+//     ds - G1 delta = -(s0 q + p3) u - s0 (q - a) delta,
+//     u = sd/r - delta = ((sin delta - delta) - delta (r - 1)) / r,
+//     r^2 - 1 = sd (2 a cd + (a^2 + b^2 - 1) sd),  q = (2 a cd + (a^2 + b^2) sd)/(cd + r).
 struct Loc {
   int m, n;
   float fa, fs, sign;
   bool ok;
 };
+
+// Row/bin split of the fractional indices and the fold of alpha into [0, pi).
+__device__ __forceinline__ Loc loc_tail(const Anchor& an, float fa, float fs, float Li, int n_alpha, int n_s) {
+  // masked samples of the other view may carry extreme offsets: clamp before the
+  // integer conversion so that no index arithmetic can overflow
+  const float mfl = fminf(fmaxf(floorf(fa), -4.0e6f), 4.0e6f);
+  const float nfl = fminf(fmaxf(floorf(fs), -4.0e6f), 4.0e6f);
+  const float lif = fminf(fmaxf(Li, -4.0e6f), 4.0e6f);
+  Loc o;
+  o.m = an.m0 + (int)mfl;
+  o.n = an.n0 + (int)lif + (int)nfl;
+  o.fa = fa - mfl;
+  o.fs = fs - nfl;
+  o.sign = an.sg;
+  if (o.m >= n_alpha || o.m < 0) {  // alpha left [0, pi): S(alpha + pi, s) = -S(alpha, -s)
+    o.m += o.m < 0 ? n_alpha : -n_alpha;
+    o.n = n_s - 2 - o.n;
+    o.fs = 1.0f - o.fs;
+    o.sign = -o.sign;
+  }
+  o.ok = o.m >= 0 && o.m < n_alpha;  // false only for a masked sample
+  return o;
+}
 
 __device__ __forceinline__ Loc locate(const Anchor& an, float cd, float sd, float jj, float de, int n_alpha,
                                       int n_s, float inv_dalpha, float inv_ds_f) {
@@ -193,34 +254,42 @@ __device__ __forceinline__ Loc locate(const Anchor& an, float cd, float sd, floa
   const float lin = an.gh * jj;  // exact
   const float Li = floorf(lin);
   const float Lf = lin - Li;     // exact
-  float fa = fmaf(dal, inv_dalpha, an.fa0);
-  float fs = (an.fs0 + Lf) + fmaf(an.gl, jj, R * inv_ds_f);
-  // masked samples of the other view may carry extreme offsets: clamp before the
-  // integer conversion so that no index arithmetic can overflow
-  const float mfl = fminf(fmaxf(floorf(fa), -4.0e6f), 4.0e6f);
-  const float nfl = fminf(fmaxf(floorf(fs), -4.0e6f), 4.0e6f);
-  const float lif = fminf(fmaxf(Li, -4.0e6f), 4.0e6f);
-  Loc o;
-  o.m = an.m0 + (int)mfl;
-  o.n = an.n0 + (int)lif + (int)nfl;
-  o.fa = fa - mfl;
-  o.fs = fs - nfl;
-  o.sign = an.sg;
-  if (o.m >= n_alpha || o.m < 0) {  // alpha left [0, pi): S(alpha + pi, s) = -S(alpha, -s)
-    o.m += o.m < 0 ? n_alpha : -n_alpha;
-    o.n = n_s - 2 - o.n;
-    o.fs = 1.0f - o.fs;
-    o.sign = -o.sign;
-  }
-  o.ok = o.m >= 0 && o.m < n_alpha;  // false only for a masked sample
-  return o;
+  const float fa = fmaf(dal, inv_dalpha, an.fa0);
+  const float fs = (an.fs0 + Lf) + fmaf(an.gl, jj, R * inv_ds_f);
+  return loc_tail(an, fa, fs, Li, n_alpha, n_s);
+}
+
+// t = tan(delta), tmd = tan(delta) - delta (accurate for small delta).
+__device__ __forceinline__ Loc locate_series(const Anchor& an, float t, float tmd, float jj, int n_alpha, int n_s) {
+  float da = an.dco[kSer - 1];
+#pragma unroll
+  for (int k = kSer - 2; k >= 0; --k) da = fmaf(da, t, an.dco[k]);
+  da *= t;
+  float sr = an.sco[kSer - 1];
+#pragma unroll
+  for (int k = kSer - 2; k >= 1; --k) sr = fmaf(sr, t, an.sco[k]);
+  sr = fmaf(an.sco[0], tmd, (t * t) * sr);
+  const float lin = an.gh * jj;  // exact
+  const float Li = floorf(lin);
+  const float Lf = lin - Li;     // exact
+  const float fa = an.fa0 + da;
+  const float fs = (an.fs0 + Lf) + fmaf(an.gl, jj, sr);
+  return loc_tail(an, fa, fs, Li, n_alpha, n_s);
+}
+
+// tan(delta) - delta: Taylor series below 0.25 (no cancellation), else direct.
+__device__ __forceinline__ float tan_minus_angle(float d, float t) {
+  const float d2 = d * d;
+  float p = fmaf(d2, 1382.0f / 155925.0f, 62.0f / 2835.0f);
+  p = fmaf(d2, p, 17.0f / 315.0f);
+  p = fmaf(d2, p, 2.0f / 15.0f);
+  p = fmaf(d2, p, 1.0f / 3.0f);
+  return fabsf(d) < 0.25f ? d * d2 * p : t - d;
 }
 
 // One sample of one view: locate it and gather the bilinear value.
 template <typename T>
-__device__ __forceinline__ float sample(const T* __restrict__ sv, int n_alpha, int n_s, const Anchor& an, float cd,
-                                        float sd, float jj, float de, float inv_dalpha, float inv_ds_f) {
-  const Loc o = locate(an, cd, sd, jj, de, n_alpha, n_s, inv_dalpha, inv_ds_f);
+__device__ __forceinline__ float sample(const T* __restrict__ sv, int n_alpha, int n_s, const Loc& o) {
   if (!o.ok) return 0.0f;
   return o.sign * bilinear(sv, n_alpha, n_s, o.m, o.fa, o.n, o.fs);
 }
@@ -232,10 +301,9 @@ __device__ __forceinline__ float sample(const T* __restrict__ sv, int n_alpha, i
 // d(alpha)/dL = (-sin a, cos a, 0)/h and d(s)/dL = -(s cos a, s sin a, 1)/h;
 // B_alpha, B_s are the slopes of the bilinear cell (piecewise constant).
 template <typename T>
-__device__ __forceinline__ float sample_grad(const T* __restrict__ sv, int n_alpha, int n_s, const Anchor& an,
-                                             float cd, float sd, float jj, float de, float inv_dalpha,
-                                             float inv_ds_f, float l0, float l1, float l2, float scale, float* g) {
-  const Loc o = locate(an, cd, sd, jj, de, n_alpha, n_s, inv_dalpha, inv_ds_f);
+__device__ __forceinline__ float sample_grad(const T* __restrict__ sv, int n_alpha, int n_s, const Loc& o,
+                                             float inv_dalpha, float inv_ds_f, float l0, float l1, float l2,
+                                             float scale, float* g) {
   const int m = o.m, n = o.n;
   const float fa = o.fa, fs = o.fs, sign = o.sign;
   g[0] = g[1] = g[2] = 0.0f;
@@ -272,7 +340,7 @@ __device__ __forceinline__ float sample_grad(const T* __restrict__ sv, int n_alp
 // FP32 operations differently (1e-7 relative, well inside the FP32 bar), while
 // each kernel is deterministic.
 template <typename T, bool GRAD>
-__device__ __forceinline__ double pair_warp(const PairArgs& g, long long p, int lane) {
+__device__ __forceinline__ double pair_warp(const PairArgs& g, long long p, int lane, float4* __restrict__ recw) {
   const PairRec* __restrict__ prs = g.prs;
   const float4* __restrict__ ctile = g.ctile;
   const int n_tiles = g.n_tiles;
@@ -313,6 +381,9 @@ __device__ __forceinline__ double pair_warp(const PairArgs& g, long long p, int 
       float sd, cd, sd_last, cd_last;
       sincosf(de_full, &sd, &cd);
       sincosf(de_last, &sd_last, &cd_last);
+      const float t_full = tanf(de_full), t_last = tanf(de_last);
+      const float tmd_full = tan_minus_angle(de_full, t_full), tmd_last = tan_minus_angle(de_last, t_last);
+      const float tan_half_tile = tanf(15.5f * dkf);
       const int r0lo = pr.r0lo, r0hi = pr.r0hi, r1lo = pr.r1lo, r1hi = pr.r1hi;
       const float4* ct = ctile + p * n_tiles;
       float Af[12];
@@ -321,25 +392,36 @@ __device__ __forceinline__ double pair_warp(const PairArgs& g, long long p, int 
         for (int i = 0; i < 12; ++i) Af[i] = (&pr.Af[0][0])[2 * i];
       }
       for (int t0 = 0; t0 < n_tiles; t0 += 16) {
-        Anchor mine;
         {
           const int v = lane >> 4;
           int t = t0 + (lane & 15);
           if (t >= n_tiles) t = n_tiles - 1;
-          mine = make_anchor(pr.Af[v], ct[t], alpha_dir, n_alpha, inv_dalpha, inv_ds, half_ns1, inv_ds_f, dk);
+          store_anchor(recw + 8 * lane, make_anchor(pr.Af[v], ct[t], alpha_dir, n_alpha, inv_dalpha, inv_ds,
+                                                    half_ns1, inv_ds_f, dk, tan_half_tile));
         }
+        __syncwarp();
         const int tmax = min(16, n_tiles - t0);
         for (int tt = 0; tt < tmax; ++tt) {
-          const Anchor aa = shfl_anchor(mine, tt);
-          const Anchor ab = shfl_anchor(mine, 16 + tt);
           const int k = 32 * (t0 + tt) + lane;
           const bool valid = k < K && ((k >= r0lo && k < r0hi) || (k >= r1lo && k < r1hi));
           const bool last = t0 + tt == n_tiles - 1;
           const float c_ = last ? cd_last : cd, s_ = last ? sd_last : sd;
           const float jj = last ? jj_last : jj_full, de = last ? de_last : de_full;
+          const float t_ = last ? t_last : t_full, tmd_ = last ? tmd_last : tmd_full;
+          Loc la, lb;
+          {
+            const Anchor an = load_anchor(recw + 8 * tt);
+            la = an.ser != 0.0f ? locate_series(an, t_, tmd_, jj, n_alpha, n_s)  // warp-uniform choice
+                                : locate(an, c_, s_, jj, de, n_alpha, n_s, inv_dalpha, inv_ds_f);
+          }
+          {
+            const Anchor an = load_anchor(recw + 8 * (16 + tt));
+            lb = an.ser != 0.0f ? locate_series(an, t_, tmd_, jj, n_alpha, n_s)
+                                : locate(an, c_, s_, jj, de, n_alpha, n_s, inv_dalpha, inv_ds_f);
+          }
           if (!GRAD) {
-            const float Sa = sca * sample(sa, n_alpha, n_s, aa, c_, s_, jj, de, inv_dalpha, inv_ds_f);
-            const float Sb = scb * sample(sb, n_alpha, n_s, ab, c_, s_, jj, de, inv_dalpha, inv_ds_f);
+            const float Sa = sca * sample(sa, n_alpha, n_s, la);
+            const float Sb = scb * sample(sb, n_alpha, n_s, lb);
             const float dd = Sa - Sb;
             acc += valid ? dd * dd : 0.0f;
           } else {
@@ -348,12 +430,10 @@ __device__ __forceinline__ double pair_warp(const PairArgs& g, long long p, int 
             const float cx = ctd.x, cy = ctd.y;
             const float ckx = cx * c_ - cy * s_, cky = cx * s_ + cy * c_;
             float ga[3], gb[3];
-            const float Sa = sample_grad(sa, n_alpha, n_s, aa, c_, s_, jj, de, inv_dalpha, inv_ds_f,
-                                         Af[0] * ckx + Af[1] * cky, Af[2] * ckx + Af[3] * cky,
-                                         Af[4] * ckx + Af[5] * cky, sca, ga);
-            const float Sb = sample_grad(sb, n_alpha, n_s, ab, c_, s_, jj, de, inv_dalpha, inv_ds_f,
-                                         Af[6] * ckx + Af[7] * cky, Af[8] * ckx + Af[9] * cky,
-                                         Af[10] * ckx + Af[11] * cky, scb, gb);
+            const float Sa = sample_grad(sa, n_alpha, n_s, la, inv_dalpha, inv_ds_f, Af[0] * ckx + Af[1] * cky,
+                                         Af[2] * ckx + Af[3] * cky, Af[4] * ckx + Af[5] * cky, sca, ga);
+            const float Sb = sample_grad(sb, n_alpha, n_s, lb, inv_dalpha, inv_ds_f, Af[6] * ckx + Af[7] * cky,
+                                         Af[8] * ckx + Af[9] * cky, Af[10] * ckx + Af[11] * cky, scb, gb);
             const float dd = Sa - Sb;
             acc += valid ? dd * dd : 0.0f;
             const float w2 = valid ? 2.0f * dd : 0.0f;
@@ -366,6 +446,7 @@ __device__ __forceinline__ double pair_warp(const PairArgs& g, long long p, int 
             }
           }
         }
+        __syncwarp();  // records are rewritten by the next chunk
       }
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -398,10 +479,11 @@ __device__ __forceinline__ double pair_warp(const PairArgs& g, long long p, int 
 // One block of kWarpsPerBlock consecutive pairs: their e summed in a fixed order
 // into partial[blk].
 template <typename T, bool GRAD>
-__device__ __forceinline__ void pair_block(const PairArgs& g, long long blk, double* e_warp) {
+__device__ __forceinline__ void pair_block(const PairArgs& g, long long blk, double* e_warp, float4* recs) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long p = blk * kWarpsPerBlock + wib;
-  const double e_val = p < g.n_pairs ? pair_warp<T, GRAD>(g, p, lane) : 0.0;  // warp-uniform
+  const double e_val =
+      p < g.n_pairs ? pair_warp<T, GRAD>(g, p, lane, recs + (size_t)wib * 32 * 8) : 0.0;  // warp-uniform
   if (lane == 0) e_warp[wib] = e_val;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -413,9 +495,10 @@ __device__ __forceinline__ void pair_block(const PairArgs& g, long long blk, dou
 }
 
 template <typename T, bool GRAD>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) ecc_pair_kernel(PairArgs g) {
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 3) ecc_pair_kernel(PairArgs g) {
   __shared__ double e_warp[kWarpsPerBlock];
-  pair_block<T, GRAD>(g, blockIdx.x, e_warp);
+  __shared__ float4 recs[kWarpsPerBlock * 32 * 8];  // anchor records, 4 KB per warp
+  pair_block<T, GRAD>(g, blockIdx.x, e_warp, recs);
 }
 
 // Fixed-order sum of n block partials by one block of 1024 threads: deterministic.
@@ -444,11 +527,12 @@ __global__ void __launch_bounds__(1024) reduce_kernel(const double* __restrict__
 // the next block index from a global counter (no waiting on other CTAs), finds its
 // job and runs the same per-block code as the single-scan kernel, so every job's
 // partials, and its total, equal those of an evaluation of the job alone.
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) serve_pair_kernel(const ServeJob* __restrict__ jobs,
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 3) serve_pair_kernel(const ServeJob* __restrict__ jobs,
                                                                          const long long* __restrict__ boff,
                                                                          int n_jobs,
                                                                          unsigned long long* __restrict__ next) {
   __shared__ double e_warp[kWarpsPerBlock];
+  __shared__ float4 recs[kWarpsPerBlock * 32 * 8];  // anchor records, 4 KB per warp
   __shared__ long long item;
   const long long total = boff[n_jobs];
   for (;;) {
@@ -462,13 +546,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) serve_pair_kernel(const S
     const long long blk = it - boff[j];
     switch (jobs[j].dtype) {
       case 0:
-        pair_block<float, true>(g, blk, e_warp);
+        pair_block<float, true>(g, blk, e_warp, recs);
         break;
       case 1:
-        pair_block<__half, true>(g, blk, e_warp);
+        pair_block<__half, true>(g, blk, e_warp, recs);
         break;
       default:
-        pair_block<__nv_bfloat16, true>(g, blk, e_warp);
+        pair_block<__nv_bfloat16, true>(g, blk, e_warp, recs);
         break;
     }
   }
