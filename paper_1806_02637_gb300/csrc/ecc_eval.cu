@@ -39,26 +39,25 @@ struct Elem<__nv_bfloat16> {
   static __device__ __forceinline__ float get(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
 };
 
-template <typename T>
-__device__ __forceinline__ float fetch(const T* __restrict__ row, int n, int n_s) {
-  return (n >= 0 && n < n_s) ? Elem<T>::get(row + n) : 0.0f;
-}
-
 // Bilinear value at alpha row m (+ fraction fa toward row m+1) and s position
 // n + fs of one view's sinogram.  Row n_alpha continues as row 0 at -s, negated.
+// A line that meets the detector lies inside the s grid (|s| <= half its diagonal),
+// so the bin is clamped to [0, n_s - 2] once instead of testing every tap: this
+// changes nothing for such lines and keeps the reads of masked samples in bounds.
 template <typename T>
 __device__ __forceinline__ float bilinear(const T* __restrict__ sv, int n_alpha, int n_s, int m, float fa, int n,
                                           float fs) {
-  const T* r0 = sv + (size_t)m * n_s;
-  const float t00 = fetch(r0, n, n_s), t01 = fetch(r0, n + 1, n_s);
+  n = min(max(n, 0), n_s - 2);
+  const T* r0 = sv + (size_t)m * n_s + n;
+  const float t00 = Elem<T>::get(r0), t01 = Elem<T>::get(r0 + 1);
   const float v0 = fmaf(fs, t01 - t00, t00);
   float v1;
   if (m + 1 < n_alpha) {
-    const T* r1 = r0 + n_s;
-    const float t10 = fetch(r1, n, n_s), t11 = fetch(r1, n + 1, n_s);
+    const float t10 = Elem<T>::get(r0 + n_s), t11 = Elem<T>::get(r0 + n_s + 1);
     v1 = fmaf(fs, t11 - t10, t10);
-  } else {
-    const float t10 = fetch(sv, n_s - 1 - n, n_s), t11 = fetch(sv, n_s - 2 - n, n_s);
+  } else {  // row 0 at bins n_s - 1 - n and n_s - 2 - n
+    const T* q = sv + (n_s - 2 - n);
+    const float t10 = Elem<T>::get(q + 1), t11 = Elem<T>::get(q);
     v1 = -fmaf(fs, t11 - t10, t10);
   }
   return fmaf(fa, v1 - v0, v0);
@@ -304,22 +303,23 @@ template <typename T>
 __device__ __forceinline__ float sample_grad(const T* __restrict__ sv, int n_alpha, int n_s, const Loc& o,
                                              float inv_dalpha, float inv_ds_f, float l0, float l1, float l2,
                                              float scale, float* g) {
-  const int m = o.m, n = o.n;
+  const int m = o.m;
+  const int n = min(max(o.n, 0), n_s - 2);  // as in bilinear()
   const float fa = o.fa, fs = o.fs, sign = o.sign;
   g[0] = g[1] = g[2] = 0.0f;
   if (!o.ok) return 0.0f;
-  const T* r0 = sv + (size_t)m * n_s;
-  const float t00 = fetch(r0, n, n_s), t01 = fetch(r0, n + 1, n_s);
+  const T* r0 = sv + (size_t)m * n_s + n;
+  const float t00 = Elem<T>::get(r0), t01 = Elem<T>::get(r0 + 1);
   const float v0 = fmaf(fs, t01 - t00, t00);
   const float dv0 = t01 - t00;
   float v1, dv1;
   if (m + 1 < n_alpha) {
-    const T* r1 = r0 + n_s;
-    const float t10 = fetch(r1, n, n_s), t11 = fetch(r1, n + 1, n_s);
+    const float t10 = Elem<T>::get(r0 + n_s), t11 = Elem<T>::get(r0 + n_s + 1);
     v1 = fmaf(fs, t11 - t10, t10);
     dv1 = t11 - t10;
-  } else {
-    const float t10 = fetch(sv, n_s - 1 - n, n_s), t11 = fetch(sv, n_s - 2 - n, n_s);
+  } else {  // row 0 at bins n_s - 1 - n and n_s - 2 - n
+    const T* q = sv + (n_s - 2 - n);
+    const float t10 = Elem<T>::get(q + 1), t11 = Elem<T>::get(q);
     v1 = -fmaf(fs, t11 - t10, t10);
     dv1 = -(t11 - t10);
   }
