@@ -219,6 +219,9 @@ int ecc_scan_consistency_host(ecc_ctx* ctx, int n_views, const double* P_host, c
  * ticket.  Pinned host memory makes the input copies asynchronous.  While jobs are
  * served, the context may still be used for the other calls from its own thread.
  */
+/* Motion models of a served job. */
+enum { ECC_MOTION_PER_VIEW = 0, ECC_MOTION_AKIMA = 1 };
+
 typedef struct ecc_job {
   int n_views;              /* >= 2 (<= 4096) */
   const double* P;          /* host FP64 [n_views][12] */
@@ -232,6 +235,20 @@ typedef struct ecc_job {
   double step;              /* step size */
   double* motion_out;       /* host FP64 [n_views][6] final theta, or NULL */
   double* totals_out;       /* host FP64 [n_iters + 1] total at theta_0 .. theta_n, or NULL */
+  /* Motion model.  ECC_MOTION_PER_VIEW: the parameters of every view are the unknowns.
+   * ECC_MOTION_AKIMA (the paper's model, Optimization section): each parameter is
+   * motion0 plus an Akima spline (Akima 1970) over the view index with n_nodes nodes
+   * at x_j = j (n_views - 1) / (n_nodes - 1); the node values (starting at 0) are the
+   * unknowns and the step applies d total / d nodes (chain rule through the spline). */
+  int motion_model;
+  int n_nodes;              /* ECC_MOTION_AKIMA: 3 .. n_views */
+  int param_mask;           /* bit k set: parameter k of (rx, ry, rz, tx, ty, tz) is estimated,
+                               the others stay at motion0; 0 means all six */
+  double* nodes_out;        /* host FP64 [n_nodes][6] final node values (ECC_MOTION_AKIMA), or NULL */
+  const double* nodes0;     /* host FP64 [n_nodes][6] initial node values, or NULL (zeros).  Where all
+                               slopes of a parameter are equal (e.g. all nodes 0) Akima's weights are
+                               0/0 and the spline has kinks; the gradient there is that of the
+                               equal-weights form t_j = (m_(j-1) + m_j) / 2. */
 } ecc_job;
 
 typedef struct ecc_result {

@@ -40,7 +40,9 @@ class _Job(ctypes.Structure):
                 ("images", ctypes.c_void_p), ("W", ctypes.c_int), ("H", ctypes.c_int), ("n_alpha", ctypes.c_int),
                 ("n_s", ctypes.c_int), ("dtype", ctypes.c_int), ("n_kappa", ctypes.c_int),
                 ("cauchy_c", ctypes.c_double), ("n_iters", ctypes.c_int), ("step", ctypes.c_double),
-                ("motion_out", ctypes.c_void_p), ("totals_out", ctypes.c_void_p)]
+                ("motion_out", ctypes.c_void_p), ("totals_out", ctypes.c_void_p), ("motion_model", ctypes.c_int),
+                ("n_nodes", ctypes.c_int), ("param_mask", ctypes.c_int), ("nodes_out", ctypes.c_void_p),
+                ("nodes0", ctypes.c_void_p)]
 
 
 class _Result(ctypes.Structure):
@@ -426,6 +428,7 @@ def ecc_profile_read(ctx: Context, stream=None, max_entries: int = 32) -> dict:
 
 # ---------------------------------------------------------------- serving
 _DT = {"float32": ECC_F32, "float16": ECC_F16, "bfloat16": ECC_BF16}
+_MODELS = {"per_view": 0, "akima": 1}
 
 
 def _host_array(a, dtype, name, shape):
@@ -445,7 +448,8 @@ def _host_array(a, dtype, name, shape):
     return a, ptr
 
 
-def _job_struct(P, images, W, H, n_alpha, n_s, n_kappa, n_iters, step, dtype, cauchy_c, motion0):
+def _job_struct(P, images, W, H, n_alpha, n_s, n_kappa, n_iters, step, dtype, cauchy_c, motion0,
+                motion_model="per_view", n_nodes=0, param_mask=0, nodes0=None):
     n = int(P.shape[0])
     P, p_ptr = _host_array(P, np.float64, "P", (n, 3, 4))
     images, i_ptr = _host_array(images, np.float32, "images", (n, H, W))
@@ -455,15 +459,23 @@ def _job_struct(P, images, W, H, n_alpha, n_s, n_kappa, n_iters, step, dtype, ca
     code = _DT[dtype] if isinstance(dtype, str) else _dtype_code(dtype)
     motion_out = np.zeros((n, 6))
     totals_out = np.zeros(int(n_iters) + 1)
+    model = _MODELS[motion_model] if isinstance(motion_model, str) else int(motion_model)
+    nodes_out = np.zeros((max(int(n_nodes), 1), 6))
+    n0_ptr = None
+    if nodes0 is not None:
+        nodes0, n0_ptr = _host_array(nodes0, np.float64, "nodes0", (int(n_nodes), 6))
     j = _Job(n, p_ptr, m_ptr, i_ptr, int(W), int(H), int(n_alpha), int(n_s), code, int(n_kappa), float(cauchy_c),
-             int(n_iters), float(step), motion_out.ctypes.data, totals_out.ctypes.data)
-    return j, (P, images, motion0, motion_out, totals_out)
+             int(n_iters), float(step), motion_out.ctypes.data, totals_out.ctypes.data, model, int(n_nodes),
+             int(param_mask), nodes_out.ctypes.data, n0_ptr)
+    return j, (P, images, motion0, motion_out, totals_out, nodes_out, nodes0)
 
 
 def ecc_job_footprint(P, images, W: int, H: int, n_alpha: int, n_s: int, n_kappa: int, n_iters: int = 20,
-                      step: float = 0.0, dtype="float32", cauchy_c: float = 0.0, motion0=None) -> int:
+                      step: float = 0.0, dtype="float32", cauchy_c: float = 0.0, motion0=None,
+                      motion_model="per_view", n_nodes: int = 0, param_mask: int = 0) -> int:
     """Device bytes the job holds while admitted."""
-    j, _ = _job_struct(P, images, W, H, n_alpha, n_s, n_kappa, n_iters, step, dtype, cauchy_c, motion0)
+    j, _ = _job_struct(P, images, W, H, n_alpha, n_s, n_kappa, n_iters, step, dtype, cauchy_c, motion0,
+                       motion_model, n_nodes, param_mask)
     b = ctypes.c_size_t(0)
     rc = load().ecc_job_footprint(ctypes.byref(j), ctypes.byref(b))
     _check(None, rc, "ecc_job_footprint")
@@ -471,11 +483,17 @@ def ecc_job_footprint(P, images, W: int, H: int, n_alpha: int, n_s: int, n_kappa
 
 
 def ecc_submit(ctx: Context, P, images, W: int, H: int, n_alpha: int, n_s: int, n_kappa: int, n_iters: int = 20,
-               step: float = 0.0, dtype="float32", cauchy_c: float = 0.0, motion0=None) -> int:
+               step: float = 0.0, dtype="float32", cauchy_c: float = 0.0, motion0=None, motion_model="per_view",
+               n_nodes: int = 0, param_mask: int = 0, nodes0=None) -> int:
     """Queues a motion-compensation job (host P [n,3,4] float64, images [n,H,W] float32,
-    optional motion0 [n,6]); returns its ticket.  The host arrays are kept alive by the
-    context until the job is polled."""
-    j, keep = _job_struct(P, images, W, H, n_alpha, n_s, n_kappa, n_iters, step, dtype, cauchy_c, motion0)
+    optional motion0 [n,6]); returns its ticket.  motion_model "per_view" estimates the
+    parameters of every view, "akima" the n_nodes node values of an Akima spline per
+    parameter over the view index (added to motion0; initial node values nodes0
+    [n_nodes, 6] or zeros); param_mask selects the estimated parameters (bits of rx,
+    ry, rz, tx, ty, tz; 0 = all).  The host arrays are kept alive by the context until
+    the job is polled."""
+    j, keep = _job_struct(P, images, W, H, n_alpha, n_s, n_kappa, n_iters, step, dtype, cauchy_c, motion0,
+                          motion_model, n_nodes, param_mask, nodes0)
     t = ctypes.c_uint64(0)
     rc = load().ecc_submit(ctx.handle, ctypes.byref(j), ctypes.byref(t))
     _check(ctx, rc, "ecc_submit")
@@ -496,6 +514,7 @@ def ecc_poll(ctx: Context, ticket: int):
     if keep is not None:
         out["motion"] = keep[3]
         out["totals"] = keep[4]
+        out["nodes"] = keep[5]
     return out
 
 

@@ -9,6 +9,7 @@
 //                     arc, the integer ranges of valid samples and the direction of
 //                     each 32-sample tile centre.
 #include "dual.cuh"
+#include "motion.cuh"
 #include "ecc_internal.cuh"
 #include "kernels.cuh"
 
@@ -532,15 +533,68 @@ __global__ void __launch_bounds__(256) serve_view_grad_kernel(const ServeJob* __
   view_grad_block((int)(i - voff[j]), J.n_views, J.pair.n_pairs, nullptr, J.gpp, J.grad, sh);
 }
 
+// Per-view jobs: theta <- theta - step * grad for the estimated parameters.
 __global__ void serve_step_kernel(const ServeJob* __restrict__ jobs, const long long* __restrict__ voff, int n_jobs,
                                   long long total) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 6 * total) return;
   const int j = serve_job_of(voff, n_jobs, i / 6);
   const ServeJob& J = jobs[j];
-  if (!J.do_grad) return;
   const long long k = i - 6 * voff[j];
+  if (!J.do_grad || J.model != kMotionPerView || !(J.mask >> (int)(k % 6) & 1)) return;
   J.theta[k] = J.theta[k] - J.step * J.grad[k];
+}
+
+// Spline jobs: theta = theta0 + Akima(nodes) for the estimated parameters, and the
+// window Jacobian of each (view, parameter).
+__global__ void serve_spline_kernel(const ServeJob* __restrict__ jobs, const long long* __restrict__ voff,
+                                    int n_jobs, long long total) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 6 * total) return;
+  const int j = serve_job_of(voff, n_jobs, i / 6);
+  const ServeJob& J = jobs[j];
+  if (J.model != kMotionAkima) return;
+  const long long k = i - 6 * voff[j];
+  const int p = (int)(k % 6);
+  const long long v = k / 6;
+  if (!(J.mask >> p & 1)) {
+    J.theta[k] = J.theta0[k];
+    return;
+  }
+  const AkimaPoint a = akima_point(J.nodes + p, 6, J.n_nodes, J.h, (double)v);
+  J.theta[k] = J.theta0[k] + a.value;
+  for (int q = 0; q < 6; ++q) J.jac[6 * k + q] = a.d[q];
+  J.jbase[k] = a.base;
+}
+
+// Spline jobs: node gradient d total / d y_(n, p) = sum over the views whose window
+// holds node n of jac * grad, summed in view order; then the step on the nodes.
+// One thread per (node, parameter) of a job, one block per job.
+__global__ void serve_node_step_kernel(const ServeJob* __restrict__ jobs) {
+  const ServeJob& J = jobs[blockIdx.x];
+  if (!J.do_grad || J.model != kMotionAkima) return;
+  for (int t = threadIdx.x; t < 6 * J.n_nodes; t += blockDim.x) {
+    const int node = t / 6, p = t % 6;
+    if (!(J.mask >> p & 1)) continue;
+    // windows [i - 2, i + 3] hold node n for intervals i in [n - 3, n + 2]: views in
+    // [(n - 3) h, (n + 3) h]
+    const long long v0 = (long long)fmax(0.0, floor((node - 3) * J.h));
+    const long long v1 = (long long)fmin((double)(J.n_views - 1), ceil((node + 3) * J.h));
+    double g = 0.0;
+    for (long long v = v0; v <= v1; ++v) {
+      const long long k = 6 * v + p;
+      const int q = node - J.jbase[k];
+      if (q >= 0 && q < 6) g += J.jac[6 * k + q] * J.grad[k];
+    }
+    J.nodes[t] = J.nodes[t] - J.step * g;
+  }
+}
+
+cudaError_t launch_serve_motion(const ServeJob* jobs, const long long* voff, int n_jobs, long long n_views,
+                                cudaStream_t stream) {
+  if (n_views > 0)
+    serve_spline_kernel<<<(unsigned)((6 * n_views + 127) / 128), 128, 0, stream>>>(jobs, voff, n_jobs, n_views);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_serve_setup(const ServeJob* jobs, const long long* voff, const long long* poff, int n_jobs,
@@ -558,6 +612,7 @@ cudaError_t launch_serve_grad(const ServeJob* jobs, const long long* voff, const
   if (n_views > 0) {
     serve_view_grad_kernel<<<(unsigned)n_views, 256, 0, stream>>>(jobs, voff, n_jobs);
     serve_step_kernel<<<(unsigned)((6 * n_views + 255) / 256), 256, 0, stream>>>(jobs, voff, n_jobs, n_views);
+    serve_node_step_kernel<<<n_jobs, 128, 0, stream>>>(jobs);
   }
   return cudaGetLastError();
 }
@@ -598,5 +653,18 @@ extern "C" int ecc_internal_setup_pair_host(int n_views, const double* P, const 
   info_out[6] = r.r1lo;
   info_out[7] = r.r1hi;
   for (int i = 0; i < 12; ++i) A_out[i] = (&r.A[0][0])[i];
+  return 0;
+}
+
+// Internal host entry point (tests only): the Akima spline point of the motion
+// model, computed by the same code as the serving kernels.
+//   y host FP64 [n] node values, h node spacing, x position; out[0] value, out[1..6]
+//   derivatives with respect to y[base .. base + 5]; *base receives base.
+extern "C" int ecc_internal_akima_host(const double* y, int n, double h, double x, double* out, int* base) {
+  if (!y || !out || !base || n < 3 || !(h > 0.0)) return -1;
+  const ecc::AkimaPoint a = ecc::akima_point(y, 1, n, h, x);
+  out[0] = a.value;
+  for (int k = 0; k < 6; ++k) out[1 + k] = a.d[k];
+  *base = a.base;
   return 0;
 }

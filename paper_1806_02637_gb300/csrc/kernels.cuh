@@ -120,6 +120,13 @@ struct ServeJob {
   double* gpp;        // [n_pairs][12]
   double* total_out;  // this round's total
   int* status;
+  // motion model: per-view (theta stepped directly) or Akima spline of node values
+  int model, n_nodes, mask;  // mask: estimated parameters (bits 0..5)
+  double h;                  // node spacing in views
+  const double* theta0;      // [n_views][6] fixed part (motion0)
+  double* nodes;             // [n_nodes][6]
+  double* jac;               // [n_views][6][6] d theta / d nodes (local window)
+  int* jbase;                // [n_views][6] first node of the window
 };
 
 __host__ __device__ inline int serve_job_of(const long long* off, int n_jobs, long long i) {
@@ -140,6 +147,10 @@ cudaError_t launch_serve_setup(const ServeJob* jobs, const long long* voff, cons
 cudaError_t launch_serve_pairs(const ServeJob* jobs, const long long* boff, int n_jobs,
                                unsigned long long* counter, int grid, cudaStream_t stream);
 int serve_pairs_blocks_per_sm();
+// Motion of the round: theta = theta0 + spline(nodes) for spline jobs (and the
+// window Jacobians); per-view jobs keep their theta.
+cudaError_t launch_serve_motion(const ServeJob* jobs, const long long* voff, int n_jobs, long long n_views,
+                                cudaStream_t stream);
 // Pair gradients, per-view gradient sums and the gradient steps.
 cudaError_t launch_serve_grad(const ServeJob* jobs, const long long* voff, const long long* poff, int n_jobs,
                               long long n_views, long long n_pairs, cudaStream_t stream);

@@ -52,7 +52,8 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 size_t elem_size(int dtype) { return dtype == ECC_F32 ? 4 : 2; }
 
 struct Layout {  // byte offsets of a job's resident and transient sections
-  size_t P, theta, grad, views, vtan, adir, sino, scales, prs, ctile, partial, Gpp, gpp, totals, status, resident;
+  size_t P, theta, grad, views, vtan, adir, sino, scales, prs, ctile, partial, Gpp, gpp, totals, status;
+  size_t theta0, nodes, jac, jbase, resident;
   size_t images, rtable, wimg, stage, transient;
   int batch;
 };
@@ -83,6 +84,11 @@ Layout layout_of(const ecc_job& j) {
   L.gpp = take(np * 12 * sizeof(double));
   L.totals = take(((size_t)j.n_iters + 1) * sizeof(double));
   L.status = take(sizeof(int));
+  L.theta0 = take(n * 6 * sizeof(double));
+  const size_t nn = j.motion_model == ECC_MOTION_AKIMA ? (size_t)j.n_nodes : 0;
+  L.nodes = take(nn * 6 * sizeof(double));
+  L.jac = take(nn ? n * 36 * sizeof(double) : 0);
+  L.jbase = take(nn ? n * 6 * sizeof(int) : 0);
   L.resident = o;
   o = 0;
   L.images = take(n * (size_t)j.W * j.H * sizeof(float));
@@ -176,9 +182,17 @@ bool admit_job(ecc_serve* S, Job* J) {
   e = cudaMemcpyAsync(R + L.P, d.P, n * 12 * sizeof(double), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {
     if (d.motion0)
-      e = cudaMemcpyAsync(R + L.theta, d.motion0, n * 6 * sizeof(double), cudaMemcpyHostToDevice, s);
+      e = cudaMemcpyAsync(R + L.theta0, d.motion0, n * 6 * sizeof(double), cudaMemcpyHostToDevice, s);
     else
-      e = cudaMemsetAsync(R + L.theta, 0, n * 6 * sizeof(double), s);
+      e = cudaMemsetAsync(R + L.theta0, 0, n * 6 * sizeof(double), s);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(R + L.theta, R + L.theta0, n * 6 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && d.motion_model == ECC_MOTION_AKIMA) {
+    if (d.nodes0)
+      e = cudaMemcpyAsync(R + L.nodes, d.nodes0, (size_t)d.n_nodes * 6 * sizeof(double), cudaMemcpyHostToDevice, s);
+    else
+      e = cudaMemsetAsync(R + L.nodes, 0, (size_t)d.n_nodes * 6 * sizeof(double), s);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(R + L.status, 0, sizeof(int), s);
   if (e == cudaSuccess)
@@ -276,6 +290,8 @@ void finish_job(ecc_serve* S, Job* J) {
   const double* theta = J->h_stage + (d.n_iters + 1);
   if (d.totals_out) std::memcpy(d.totals_out, totals, sizeof(double) * (d.n_iters + 1));
   if (d.motion_out) std::memcpy(d.motion_out, theta, sizeof(double) * 6 * d.n_views);
+  if (d.motion_model == ECC_MOTION_AKIMA && d.nodes_out)
+    std::memcpy(d.nodes_out, theta + 6 * d.n_views, sizeof(double) * 6 * d.n_nodes);
   J->t_done = Clock::now();
   ecc_result& r = J->res;
   r.iters = d.n_iters;
@@ -384,6 +400,14 @@ void round_loop(ecc_serve* S) {
       s.gpp = (double*)(R + L.gpp);
       s.total_out = (double*)(R + L.totals) + J->rounds;
       s.status = (int*)(R + L.status);
+      s.model = d.motion_model;
+      s.n_nodes = d.motion_model == ECC_MOTION_AKIMA ? d.n_nodes : 0;
+      s.mask = d.param_mask ? d.param_mask : 0x3F;
+      s.h = s.n_nodes > 1 ? (double)(d.n_views - 1) / (s.n_nodes - 1) : 1.0;
+      s.theta0 = (const double*)(R + L.theta0);
+      s.nodes = (double*)(R + L.nodes);
+      s.jac = (double*)(R + L.jac);
+      s.jbase = (int*)(R + L.jbase);
       voff[i + 1] = voff[i] + n;
       poff[i + 1] = poff[i] + np;
       boff[i + 1] = boff[i] + (np + kWarpsPerPairBlock - 1) / kWarpsPerPairBlock;
@@ -396,6 +420,7 @@ void round_loop(ecc_serve* S) {
     cudaError_t e = cudaMemcpyAsync(dj, H, sizeof(ecc::ServeJob) * nj, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(dvoff, voff, sizeof(long long) * 3 * (kMaxActive + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = ecc::launch_serve_motion(dj, dvoff, nj, voff[nj], s);
     if (e == cudaSuccess) e = ecc::launch_serve_setup(dj, dvoff, dpoff, nj, voff[nj], poff[nj], s);
     if (e == cudaSuccess) e = ecc::launch_serve_pairs(dj, dboff, nj, S->d_counter + b, S->pair_grid, s);
     if (e == cudaSuccess) e = ecc::launch_serve_grad(dj, dvoff, dpoff, nj, voff[nj], poff[nj], s);
@@ -415,6 +440,9 @@ void round_loop(ecc_serve* S) {
                         s);
         cudaMemcpyAsync(J->h_stage + (d.n_iters + 1), J->dev + J->L.theta, sizeof(double) * 6 * d.n_views,
                         cudaMemcpyDeviceToHost, s);
+        if (d.motion_model == ECC_MOTION_AKIMA)
+          cudaMemcpyAsync(J->h_stage + (d.n_iters + 1) + 6 * d.n_views, J->dev + J->L.nodes,
+                          sizeof(double) * 6 * d.n_nodes, cudaMemcpyDeviceToHost, s);
         if (!J->done) cudaEventCreateWithFlags(&J->done, cudaEventDisableTiming);
         cudaEventRecord(J->done, s);
         J->st = State::Finishing;
@@ -445,8 +473,13 @@ int check_job(const ecc_job* j, std::string* why) {
   if (j->n_kappa < 1 || j->n_kappa > 65536) return bad("n_kappa out of range [1, 65536]");
   if (j->n_iters < 0 || j->n_iters > kMaxIters) return bad("n_iters out of range");
   if (!std::isfinite(j->step) || !std::isfinite(j->cauchy_c)) return bad("step or cauchy_c is not finite");
-  if (sizeof(double) * ((size_t)j->n_iters + 1 + 6 * (size_t)j->n_views) > kSlotBytes)
-    return bad("n_iters + 6 n_views too large for the result staging");
+  if (j->motion_model != ECC_MOTION_PER_VIEW && j->motion_model != ECC_MOTION_AKIMA) return bad("unknown motion_model");
+  if (j->motion_model == ECC_MOTION_AKIMA && (j->n_nodes < 3 || j->n_nodes > j->n_views))
+    return bad("n_nodes out of range [3, n_views] for the Akima motion model");
+  if (j->param_mask < 0 || j->param_mask > 0x3F) return bad("param_mask has bits beyond the six parameters");
+  const size_t nn = j->motion_model == ECC_MOTION_AKIMA ? (size_t)j->n_nodes : 0;
+  if (sizeof(double) * ((size_t)j->n_iters + 1 + 6 * (size_t)j->n_views + 6 * nn) > kSlotBytes)
+    return bad("n_iters + 6 n_views + 6 n_nodes too large for the result staging");
   return ECC_OK;
 }
 
