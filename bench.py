@@ -34,6 +34,7 @@ import synth  # noqa: E402
 METRIC = "ECC line-pair samples/s"
 UNIT = "line-pair samples/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+L1_PEAK_TBS = 128.0 * 152 * 2.07e9 / 1e12  # L1 data bytes per second (unit counts x max SM clock)
 FLOPS_PER_TAP = 4                                    # lerp (sub + fma) + accumulate
 
 
@@ -440,7 +441,14 @@ def run_ours(args):
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a 32-view launch, "
                                   f"scaled to {views_per_launch:.1f} views per launch",
                 "peak_source": "FP32 lanes x FMA x max SM clock (152 x 128 x 2 x 2.07 GHz)",
-                "work": f"{FLOPS_PER_TAP} FLOP per in-image Joseph tap, {taps} taps per step"}
+                "work": f"{FLOPS_PER_TAP} FLOP per in-image Joseph tap, {taps} taps per step",
+                # the kernel's actual limiter (ncu: L1 data-pipe wavefronts): the 8-byte
+                # interpolation pair each tap reads, against the L1 data rate
+                "l1_gather": {"achieved_tbs": 8.0 * taps * args.steps / n_dom / (ms_dom / n_dom / 1e3) / 1e12,
+                              "peak_tbs": L1_PEAK_TBS,
+                              "frac": 8.0 * taps * args.steps / n_dom / (ms_dom / n_dom / 1e3) / 1e12 / L1_PEAK_TBS,
+                              "peak_source": "128 B per clock per SM x 152 SMs x 2.07 GHz",
+                              "work": "8 B (one interpolation pair) per in-image tap"}}
     else:
         bytes_per_launch = 32.0 * units * args.steps / n_dom
         achieved = bytes_per_launch / (ms_dom / n_dom / 1e3) / 1e9

@@ -105,6 +105,14 @@ def test_ecc_parity_c1_exact_and_moved():
     _check_pairs(sc["P"], S32, cfg.W, cfg.H, cfg.K, c=1e-3, motion=th)
 
 
+def test_ecc_parity_maximum_kappa():
+    """n_kappa at the API maximum (65536 planes, 2048 tiles) on the two-view scan."""
+    cfg = synth.CONFIGS["c1"]
+    sc = H.scan("c1")
+    S32 = H.oracle_sino("c1").astype(np.float32)
+    _check_pairs(sc["P"], S32, cfg.W, cfg.H, 65536)
+
+
 SUB = tuple(range(0, 496, 21))  # 24 views of the 496-view short scan
 
 
@@ -150,6 +158,8 @@ def test_full_size_launch_sampled_pairs():
     S_all, _ = _gpu_sino(full, cfg.n_alpha, cfg.n_s)
     S_or = H.oracle_sino("c2", tuple(sorted(views))).astype(np.float32)
     idx = torch.tensor(sorted(views), device="cuda")
+    # the full-size precompute (batched launches) on the sampled views
+    assert H.sino_rel_err(S_all[idx].cpu().numpy(), S_or).max() <= H.TOL_F32
     S_all[idx] = _cuda(S_or)
     total, pp, nk = _gpu_eval(full["P"], S_all, cfg.W, cfg.H, cfg.K)
     sv = np.array(sorted(views))
