@@ -171,3 +171,27 @@ def test_served_totals_match_oracle():
         E = H.energies(sc["P"], S, cfg.W, cfg.H, cfg.K, ref["pairs"], theta)
         bound = H.TOL_F32 * np.maximum(ref["e"], H.FLOOR * E).sum()
         assert abs(total - ref["total"]) <= bound, (total, ref["total"], bound)
+
+
+def test_destroy_with_jobs_in_flight():
+    """Destroying the context while jobs are queued and running drops them and returns
+    (the scheduler threads stop after the GPU work already issued); a new context
+    serves normally afterwards.  Unknown tickets are refused."""
+    import paper_1806_02637_gb300 as ecc
+    cfg, dtype, iters, step, c, mot = JOBS["A"]
+    sc = _scan("A")
+    ctx = ecc.Context(0)
+    for _ in range(6):
+        ecc.ecc_submit(ctx, sc["P"], sc["images"], cfg.W, cfg.H, cfg.n_alpha, cfg.n_s, cfg.K, n_iters=500,
+                       step=step)
+    time.sleep(0.05)
+    t0 = time.time()
+    ctx.close()
+    assert time.time() - t0 < 30.0
+    alone, _ = _alone()
+    ctx = ecc.Context(0)
+    with pytest.raises(ecc.EccError, match=r"\(-1\)"):
+        ecc.ecc_poll(ctx, 12345)
+    out = _wait(ctx, {"A": _submit(ctx, "A")})
+    assert np.array_equal(out["A"]["totals"], alone["A"]["totals"])
+    ctx.close()
