@@ -16,8 +16,10 @@
  *     Joseph's method, half-step central difference in s, (D^2 + s^2)/D^2 weight;
  *   - the pair inconsistency d (Eq. 15), the Cauchy norm e (Eq. 16) and the sum
  *     over pairs (Eq. 17);
- *   - the gradient of that sum with respect to per-view rigid motion parameters
- *     by complex-step differentiation of the same code (no hand derivation).
+ *   - the gradient of that sum with respect to per-view rigid motion parameters,
+ *     or to the entries of each view's projection matrix (geometric calibration,
+ *     Introduction), by complex-step differentiation of the same code (no hand
+ *     derivation).
  * Readings of the paper where it is silent are listed in the repository's design
  * notes; the ones that fix arithmetic are restated beside the code below.
  *
@@ -367,7 +369,8 @@ typedef struct {
     int* mismatch;
     int* status;
     view_t_r* views;
-    double* grad_pp; /* per pair 12 partials (gradient mode) */
+    double* grad_pp; /* per pair 2 * npv partials (gradient mode) */
+    int wrt_P;       /* gradient with respect to: 0 theta (npv = 6), 1 the entries of P (npv = 12) */
 } ecc_ctx_t;
 
 static void setup_view_job(void* vctx, long lam) {
@@ -470,12 +473,44 @@ static void to_complex_view(const view_t_r* r, view_t_c* z) {
     for (int i = 0; i < 3; ++i) { z->C[i] = r->C[i]; z->up[i] = r->up[i]; }
 }
 
+/* The first three rows of T(theta) = [R t; 0 1]: the motion model applied to P = [I | 0]. */
+static void motion_rows(const double* th, double T[12]) {
+    static const double I34[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
+    static const double zero[6] = {0, 0, 0, 0, 0, 0};
+    apply_motion_r(I34, th ? th : zero, T);
+}
+
+/* Moved projection of a view whose parameter j is stepped by i*CSTEP: theta_j
+ * (wrt_P = 0) or the entry P_j of the unmoved matrix (wrt_P = 1, P' = P T(theta)). */
+static void stepped_projection(const ecc_ctx_t* c, int lam, int j, double complex Pm[12]) {
+    const double* th = c->motion ? c->motion + 6 * lam : NULL;
+    if (!c->wrt_P) {
+        double complex tz[6];
+        for (int i = 0; i < 6; ++i) tz[i] = th ? th[i] : 0.0;
+        tz[j] += I * CSTEP;
+        apply_motion_c(c->P + 12 * lam, tz, Pm);
+        return;
+    }
+    double T[12];
+    motion_rows(th, T);
+    double complex Pz[12];
+    for (int i = 0; i < 12; ++i) Pz[i] = c->P[12 * lam + i];
+    Pz[j] += I * CSTEP;
+    for (int r = 0; r < 3; ++r)
+        for (int col = 0; col < 4; ++col) {
+            double complex acc = col == 3 ? Pz[4 * r + 3] : 0.0; /* row 4 of T is (0, 0, 0, 1) */
+            for (int k = 0; k < 3; ++k) acc += Pz[4 * r + k] * T[4 * k + col];
+            Pm[4 * r + col] = acc;
+        }
+}
+
 static void grad_pair_job(void* vctx, long p) {
     ecc_ctx_t* c = (ecc_ctx_t*)vctx;
+    const int npv = c->wrt_P ? 12 : 6;
     int ab[2] = {c->pairs[2 * p], c->pairs[2 * p + 1]};
     double* arcs = c->arcs + 5 * p;
-    double* gp = c->grad_pp + 12 * p;
-    for (int i = 0; i < 12; ++i) gp[i] = 0.0;
+    double* gp = c->grad_pp + 2 * npv * p;
+    for (int i = 0; i < 2 * npv; ++i) gp[i] = 0.0;
     if (c->arcs_in) memcpy(arcs, c->arcs_in + 5 * p, 5 * sizeof(double));
     else if (pair_arcs(&c->views[ab[0]], &c->views[ab[1]], c->W, c->H, arcs) != 0) {
         c->status[p + 1] = -1;
@@ -499,13 +534,10 @@ static void grad_pair_job(void* vctx, long p) {
     }
     for (int side = 0; side < 2; ++side) {
         int lam = ab[side];
-        for (int j = 0; j < 6; ++j) {
+        for (int j = 0; j < npv; ++j) {
             view_t_c zv[2];
-            double complex th[6];
-            for (int i = 0; i < 6; ++i) th[i] = c->motion ? c->motion[6 * lam + i] : 0.0;
-            th[j] += I * CSTEP;
             double complex Pm[12];
-            apply_motion_c(c->P + 12 * lam, th, Pm);
+            stepped_projection(c, lam, j, Pm);
             if (view_setup_P_c(Pm, &zv[side]) != 0) {
                 c->status[p + 1] = -1;
                 return;
@@ -520,18 +552,16 @@ static void grad_pair_job(void* vctx, long p) {
             }
             double complex d = nk > 0 ? sum / nk : 0.0;
             double complex e = c->c > 0 ? d / (1.0 + d / c->c) : d;
-            gp[6 * side + j] = cimag(e) / CSTEP;
+            gp[npv * side + j] = cimag(e) / CSTEP;
         }
     }
 }
 
-/* Gradient of the total (Eq. 17) with respect to theta [n_views][6], with the
- * sampled arcs and the validity mask frozen at the evaluation point (or given in
- * arcs_in).  Also returns d, e, N_kappa per pair and the total. */
-int orc_ecc_grad(int n_views, const double* P, const double* motion, const double* sino, int W, int H, int n_alpha,
-                 int n_s, int K, double cauchy_c, const int* pairs, int n_pairs, int construction,
-                 const double* arcs_in, int n_threads, double* d, double* e, int* nk, double* arcs_out, double* total,
-                 double* grad) {
+static int ecc_grad_impl(int n_views, const double* P, const double* motion, const double* sino, int W, int H,
+                         int n_alpha, int n_s, int K, double cauchy_c, const int* pairs, int n_pairs,
+                         int construction, const double* arcs_in, int n_threads, int wrt_P, double* d, double* e,
+                         int* nk, double* arcs_out, double* total, double* grad) {
+    const int npv = wrt_P ? 12 : 6;
     int* own = NULL;
     if (!pairs) {
         own = all_pairs(n_views, &n_pairs);
@@ -542,22 +572,22 @@ int orc_ecc_grad(int n_views, const double* P, const double* motion, const doubl
     c.n_views = n_views; c.P = P; c.motion = motion; c.sino = sino;
     c.W = W; c.H = H; c.n_alpha = n_alpha; c.n_s = n_s; c.K = K; c.c = cauchy_c;
     c.pairs = pairs; c.construction = construction; c.arcs_in = arcs_in;
-    c.arcs = arcs_out; c.d = d; c.e = e; c.nk = nk;
+    c.arcs = arcs_out; c.d = d; c.e = e; c.nk = nk; c.wrt_P = wrt_P;
     c.status = (int*)calloc((size_t)n_pairs + 1, sizeof(int));
     c.views = (view_t_r*)malloc(sizeof(view_t_r) * (size_t)(n_views > 0 ? n_views : 1));
-    c.grad_pp = (double*)malloc(sizeof(double) * 12 * (size_t)(n_pairs > 0 ? n_pairs : 1));
+    c.grad_pp = (double*)malloc(sizeof(double) * 2 * npv * (size_t)(n_pairs > 0 ? n_pairs : 1));
     orc_parallel_for(n_views, n_threads, setup_view_job, &c);
     int bad = 0;
     if (c.status[0] != 0) bad = 1;
     else orc_parallel_for(n_pairs, n_threads, grad_pair_job, &c);
-    memset(grad, 0, sizeof(double) * 6 * (size_t)n_views);
+    memset(grad, 0, sizeof(double) * npv * (size_t)n_views);
     double t = 0.0;
     for (int p = 0; p < n_pairs && !bad; ++p) {
         if (c.status[p + 1] != 0) { --bad; continue; }
         t += e[p];
-        for (int j = 0; j < 6; ++j) {
-            grad[6 * pairs[2 * p] + j] += c.grad_pp[12 * p + j];
-            grad[6 * pairs[2 * p + 1] + j] += c.grad_pp[12 * p + 6 + j];
+        for (int j = 0; j < npv; ++j) {
+            grad[npv * pairs[2 * p] + j] += c.grad_pp[2 * npv * p + j];
+            grad[npv * pairs[2 * p + 1] + j] += c.grad_pp[2 * npv * p + npv + j];
         }
     }
     *total = t;
@@ -566,4 +596,26 @@ int orc_ecc_grad(int n_views, const double* P, const double* motion, const doubl
     free(c.grad_pp);
     free(own);
     return bad > 0 ? -1 : bad;
+}
+
+/* Gradient of the total (Eq. 17) with respect to theta [n_views][6], with the
+ * sampled arcs and the validity mask frozen at the evaluation point (or given in
+ * arcs_in).  Also returns d, e, N_kappa per pair and the total. */
+int orc_ecc_grad(int n_views, const double* P, const double* motion, const double* sino, int W, int H, int n_alpha,
+                 int n_s, int K, double cauchy_c, const int* pairs, int n_pairs, int construction,
+                 const double* arcs_in, int n_threads, double* d, double* e, int* nk, double* arcs_out, double* total,
+                 double* grad) {
+    return ecc_grad_impl(n_views, P, motion, sino, W, H, n_alpha, n_s, K, cauchy_c, pairs, n_pairs, construction,
+                         arcs_in, n_threads, 0, d, e, nk, arcs_out, total, grad);
+}
+
+/* As orc_ecc_grad, with respect to the entries of each view's projection matrix:
+ * grad_P [n_views][12] = d total / d P (the matrix before the view's motion; the
+ * view uses P T(theta)).  Geometric calibration by the consistency (Introduction). */
+int orc_ecc_grad_P(int n_views, const double* P, const double* motion, const double* sino, int W, int H,
+                   int n_alpha, int n_s, int K, double cauchy_c, const int* pairs, int n_pairs, int construction,
+                   const double* arcs_in, int n_threads, double* d, double* e, int* nk, double* arcs_out,
+                   double* total, double* grad_P) {
+    return ecc_grad_impl(n_views, P, motion, sino, W, H, n_alpha, n_s, K, cauchy_c, pairs, n_pairs, construction,
+                         arcs_in, n_threads, 1, d, e, nk, arcs_out, total, grad_P);
 }

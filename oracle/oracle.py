@@ -70,6 +70,8 @@ def _load():
             lib.orc_ecc.restype = ctypes.c_int
             lib.orc_ecc_grad.argtypes = ecc_args + [_dp, _dp]
             lib.orc_ecc_grad.restype = ctypes.c_int
+            lib.orc_ecc_grad_P.argtypes = ecc_args + [_dp, _dp]
+            lib.orc_ecc_grad_P.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -216,10 +218,7 @@ def ecc(P, sino, W: int, H: int, K: int, cauchy_c: float = 0.0, motion=None, pai
     return {"d": d, "e": e, "nk": nk, "arcs": arcs_out, "mismatch": mm, "total": total.value, "pairs": pr}
 
 
-def ecc_grad(P, sino, W: int, H: int, K: int, cauchy_c: float = 0.0, motion=None, pairs=None,
-             construction: str = "inf", arcs=None, n_threads=None) -> dict:
-    """Gradient of the total w.r.t. per-view motion [n_views, 6] by complex-step
-    differentiation, arcs and validity frozen at the evaluation point."""
+def _grad(fn, npv, P, sino, W, H, K, cauchy_c, motion, pairs, construction, arcs, n_threads):
     P = _d(P).reshape(-1, 12)
     nv = P.shape[0]
     sino = _d(sino)
@@ -230,13 +229,29 @@ def ecc_grad(P, sino, W: int, H: int, K: int, cauchy_c: float = 0.0, motion=None
     d, e = np.zeros(npairs), np.zeros(npairs)
     nk = np.zeros(npairs, dtype=np.int32)
     arcs_out = np.zeros((npairs, 5))
-    grad = np.zeros((nv, 6))
+    grad = np.zeros((nv, npv))
     total = ctypes.c_double(0.0)
     cons = {"inf": 0, "pinv": 1}[construction]
-    rc = _load().orc_ecc_grad(nv, _ptr(P), _ptr(mot), _ptr(sino), int(W), int(H), sino.shape[1], sino.shape[2],
-                              int(K), float(cauchy_c), _ptr(pr, _ip), npairs, cons, _ptr(arcs_in),
-                              _threads(n_threads), _ptr(d), _ptr(e), _ptr(nk, _ip), _ptr(arcs_out),
-                              ctypes.byref(total), _ptr(grad))
+    rc = fn(nv, _ptr(P), _ptr(mot), _ptr(sino), int(W), int(H), sino.shape[1], sino.shape[2], int(K),
+            float(cauchy_c), _ptr(pr, _ip), npairs, cons, _ptr(arcs_in), _threads(n_threads), _ptr(d), _ptr(e),
+            _ptr(nk, _ip), _ptr(arcs_out), ctypes.byref(total), _ptr(grad))
     if rc != 0:
-        raise RuntimeError(f"orc_ecc_grad failed ({rc})")
+        raise RuntimeError(f"oracle gradient failed ({rc})")
     return {"d": d, "e": e, "nk": nk, "arcs": arcs_out, "total": total.value, "grad": grad, "pairs": pr}
+
+
+def ecc_grad(P, sino, W: int, H: int, K: int, cauchy_c: float = 0.0, motion=None, pairs=None,
+             construction: str = "inf", arcs=None, n_threads=None) -> dict:
+    """Gradient of the total w.r.t. per-view motion [n_views, 6] by complex-step
+    differentiation, arcs and validity frozen at the evaluation point."""
+    return _grad(_load().orc_ecc_grad, 6, P, sino, W, H, K, cauchy_c, motion, pairs, construction, arcs, n_threads)
+
+
+def ecc_grad_P(P, sino, W: int, H: int, K: int, cauchy_c: float = 0.0, motion=None, pairs=None,
+               construction: str = "inf", arcs=None, n_threads=None) -> dict:
+    """Gradient of the total w.r.t. the entries of each view's projection matrix
+    ("grad" [n_views, 12], row-major like P; the view uses P T(theta)) by
+    complex-step differentiation, arcs and validity frozen at the evaluation point:
+    geometric calibration by the consistency (Introduction)."""
+    return _grad(_load().orc_ecc_grad_P, 12, P, sino, W, H, K, cauchy_c, motion, pairs, construction, arcs,
+                 n_threads)
