@@ -176,6 +176,26 @@ int ecc_evaluate_grad(ecc_ctx* ctx, int n_views, const double* P, const double* 
                       int32_t* nkappa, double* grad, void* stream);
 
 /*
+ * Geometric calibration by the consistency (the Introduction names calibration as
+ * a use of the epipolar consistency; Eq. 17 as the objective): as ecc_evaluate,
+ * plus the gradient of the total with respect to the entries of each view's
+ * projection matrix, with the sampled planes held at the evaluation point:
+ *   grad_P device FP64 [n_views][12] = d total / d P, row-major like P.
+ * It is the derivative with respect to the P passed in; with motion the view uses
+ * P T(theta), so grad_P = (d total / d P') T(theta)^T.  The total is invariant
+ * under P -> s P for each view, so sum_ij P_ij grad_P_ij = 0 per view (to
+ * rounding); a step along grad_P changes the scale of P, which the evaluation
+ * ignores.  The per-pair part reads the pair kernel's d e / d A, as
+ * ecc_evaluate_grad; the chain through the pencil frame, the sources and the
+ * cofactor matrices to P is FP64 (forward-mode tangents), summed per view in a
+ * fixed order.  Errors as ecc_evaluate; ECC_EINVAL if grad_P is NULL.
+ */
+int ecc_evaluate_grad_projection(ecc_ctx* ctx, int n_views, const double* P, const double* motion, const void* sino,
+                                 const float* scales, int W, int H, int n_alpha, int n_s, int dtype, int n_kappa,
+                                 double cauchy_c, const int32_t* pairs, int n_pairs, double* total,
+                                 double* per_pair, int32_t* nkappa, double* grad_P, void* stream);
+
+/*
  * As ecc_evaluate, but the planes of every pair (kappa arcs, step and validity
  * mask) are those sampled by the previous ecc_evaluate / ecc_evaluate_grad call on
  * this context; only the geometry (P, motion) may change.  The arguments n_views,

@@ -22,7 +22,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["EccError", "Context", "library_path", "load", "ecc_precompute_radon_derivative", "ecc_evaluate",
-           "ecc_evaluate_grad", "ecc_evaluate_frozen", "ecc_evaluate_noalloc", "consistency",
+           "ecc_evaluate_grad", "ecc_evaluate_grad_projection", "ecc_evaluate_frozen", "ecc_evaluate_noalloc", "consistency",
            "ecc_scan_consistency_host", "ecc_status", "ecc_kernel_launches", "ecc_profile_enable",
            "ecc_profile_read", "ecc_job_footprint", "ecc_submit", "ecc_poll", "ecc_serve_stats",
            "ECC_F32", "ECC_F16", "ECC_BF16"]
@@ -88,6 +88,9 @@ def load(build_if_missing: bool = True):
         lib.ecc_scan_consistency_host.restype = i
         lib.ecc_evaluate_grad.argtypes = [vp, i, vp, vp, vp, vp, i, i, i, i, i, i, d, vp, i, vp, vp, vp, vp, vp]
         lib.ecc_evaluate_grad.restype = i
+        lib.ecc_evaluate_grad_projection.argtypes = [vp, i, vp, vp, vp, vp, i, i, i, i, i, i, d, vp, i, vp, vp, vp,
+                                                     vp, vp]
+        lib.ecc_evaluate_grad_projection.restype = i
         lib.ecc_evaluate_noalloc.argtypes = [i, vp, vp, vp, vp, i, i, i, i, i, i, d, vp, i, vp, vp, vp, vp,
                                              ctypes.c_char_p, sz]
         lib.ecc_evaluate_noalloc.restype = i
@@ -328,6 +331,26 @@ def ecc_evaluate_grad(ctx: Context, P, sino, W: int, H: int, n_kappa: int, cauch
                                   _stream(stream))
     _check(ctx, rc, "ecc_evaluate_grad")
     return {"total": total, "per_pair": per_pair, "nkappa": nkappa, "grad": grad}
+
+
+def ecc_evaluate_grad_projection(ctx: Context, P, sino, W: int, H: int, n_kappa: int, cauchy_c: float = 0.0,
+                                 motion=None, pairs=None, scales=None, total=None, per_pair=None, nkappa=None,
+                                 grad_P=None, want_per_pair: bool = True, stream=None) -> dict:
+    """As ecc_evaluate plus grad_P [N, 12] float64 = d total / d P (entries of each
+    view's projection matrix, row-major; sampled planes held at the evaluation
+    point): geometric calibration by the consistency."""
+    torch = _torch()
+    code, N, P, sino, motion, pairs, n_pairs, scales, total, per_pair, nkappa = _eval_args(
+        P, sino, motion, pairs, scales, total, per_pair, nkappa, want_per_pair)
+    if grad_P is None:
+        grad_P = torch.empty((N, 12), dtype=torch.float64, device=sino.device)
+    _dev(grad_P, torch.float64, "grad_P", (N, 12))
+    rc = load().ecc_evaluate_grad_projection(ctx.handle, N, _ptr(P), _ptr(motion), _ptr(sino), _ptr(scales),
+                                             int(W), int(H), sino.shape[1], sino.shape[2], code, int(n_kappa),
+                                             float(cauchy_c), _ptr(pairs), int(n_pairs), _ptr(total),
+                                             _ptr(per_pair), _ptr(nkappa), _ptr(grad_P), _stream(stream))
+    _check(ctx, rc, "ecc_evaluate_grad_projection")
+    return {"total": total, "per_pair": per_pair, "nkappa": nkappa, "grad_P": grad_P}
 
 
 def _autograd_function():

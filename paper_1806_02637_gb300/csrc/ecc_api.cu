@@ -43,6 +43,7 @@ struct ecc_ctx {
   int* d_status = nullptr;
   Buf views, pairs, ctile, adir, perpair, nk, partial, rtable, wimg, stage;
   Buf vtan, Gpp, gpp;  // adjoint scratch
+  Buf vtanP, gq;       // adjoint scratch of the gradient with respect to P
   // sampling of the last evaluation (for ecc_evaluate_frozen)
   bool samp_valid = false;
   int samp_views = 0, samp_pairs = 0, samp_K = 0, samp_W = 0, samp_H = 0;
@@ -185,7 +186,7 @@ int run_precompute(ecc_ctx* c, int n_views, const double* P, const float* images
 int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion, const void* sino,
                  const float* scales, int W, int H, int n_alpha, int n_s, int dtype, int n_kappa, double cauchy_c,
                  const int32_t* pairs, int n_pairs, double* total, double* per_pair, int32_t* nkappa, double* grad,
-                 bool reuse, cudaStream_t s) {
+                 double* grad_P, bool reuse, cudaStream_t s) {
   int rc;
   cudaError_t e;
   if (reuse && !(c->samp_valid && c->samp_views == n_views && c->samp_pairs == n_pairs && c->samp_K == n_kappa &&
@@ -194,6 +195,10 @@ int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion,
   if (grad && n_pairs == 0) {
     e = cudaMemsetAsync(grad, 0, sizeof(double) * 6 * (size_t)n_views, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "memset grad");
+  }
+  if (grad_P && n_pairs == 0) {
+    e = cudaMemsetAsync(grad_P, 0, sizeof(double) * 12 * (size_t)n_views, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "memset grad_P");
   }
   if (n_pairs == 0) {
     e = cudaMemsetAsync(total, 0, sizeof(double), s);
@@ -211,10 +216,16 @@ int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion,
     if ((rc = ensure(c, c->perpair, sizeof(double) * 2 * (size_t)np, "per-pair")) != ECC_OK) return rc;
     per_pair = (double*)c->perpair.p;
   }
+  if (grad || grad_P) {
+    if ((rc = ensure(c, c->Gpp, sizeof(double) * 12 * (size_t)np, "pair adjoints")) != ECC_OK) return rc;
+  }
   if (grad) {
     if ((rc = ensure(c, c->vtan, sizeof(ecc::ViewTan) * (size_t)n_views, "view tangents")) != ECC_OK) return rc;
-    if ((rc = ensure(c, c->Gpp, sizeof(double) * 12 * (size_t)np, "pair adjoints")) != ECC_OK) return rc;
     if ((rc = ensure(c, c->gpp, sizeof(double) * 12 * (size_t)np, "pair gradients")) != ECC_OK) return rc;
+  }
+  if (grad_P) {
+    if ((rc = ensure(c, c->vtanP, sizeof(ecc::ViewTanP) * (size_t)n_views, "view P tangents")) != ECC_OK) return rc;
+    if ((rc = ensure(c, c->gq, sizeof(double) * 30 * (size_t)np, "pair q gradients")) != ECC_OK) return rc;
   }
   if (!reuse) c->samp_valid = false;
   const ecc::LaunchHooks hk = hooks_of(c);
@@ -236,8 +247,8 @@ int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion,
   int nb = 0;
   e = ecc::launch_ecc_pairs(np, (const ecc::PairRec*)c->pairs.p, (const float4*)c->ctile.p, n_tiles,
                             (const float4*)c->adir.p, sino, scales, dtype, n_alpha, n_s, n_kappa, W, H, cauchy_c,
-                            per_pair, nkappa, (double*)c->partial.p, grad ? (double*)c->Gpp.p : nullptr, &nb, hk,
-                            s);
+                            per_pair, nkappa, (double*)c->partial.p, (grad || grad_P) ? (double*)c->Gpp.p : nullptr,
+                            &nb, hk, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "pair kernel launch");
   e = ecc::launch_reduce((const double*)c->partial.p, nb, total, hk, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "reduce launch");
@@ -258,6 +269,24 @@ int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion,
     ecc::view_grad_reduce_kernel<<<n_views, 256, 0, s>>>(n_views, np, pairs, (const double*)c->gpp.p, grad);
     hk.on_end("view_grad_reduce_kernel", s);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "gradient reduce launch");
+  }
+  if (grad_P) {
+    hk.on_begin("view_tangent_P_kernel", s);
+    ecc::view_tangent_P_kernel<<<(12 * n_views + 95) / 96, 96, 0, s>>>(n_views, P, motion, W, H,
+                                                                       (ecc::ViewTanP*)c->vtanP.p);
+    hk.on_end("view_tangent_P_kernel", s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "view P tangent launch");
+    hk.on_begin("pair_grad_q_kernel", s);
+    ecc::pair_grad_q_kernel<<<(unsigned)((np + 63) / 64), 64, 0, s>>>(np, (const ecc::PairRec*)c->pairs.p,
+                                                                      (const ecc::ViewRec*)c->views.p,
+                                                                      (const double*)c->Gpp.p, (double*)c->gq.p);
+    hk.on_end("pair_grad_q_kernel", s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "pair q gradient launch");
+    hk.on_begin("view_grad_P_kernel", s);
+    ecc::view_grad_P_kernel<<<n_views, 256, 0, s>>>(n_views, np, pairs, (const double*)c->gq.p,
+                                                    (const ecc::ViewTanP*)c->vtanP.p, grad_P);
+    hk.on_end("view_grad_P_kernel", s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "P gradient reduce launch");
   }
   if (!reuse) {
     c->samp_valid = true;
@@ -308,7 +337,7 @@ void ecc_destroy(ecc_ctx* c) {
   ecc::serve_destroy(c->serve);
   cudaDeviceSynchronize();
   Buf* bufs[] = {&c->views, &c->pairs, &c->ctile, &c->adir, &c->perpair, &c->nk, &c->partial, &c->rtable, &c->wimg,
-                 &c->vtan, &c->Gpp, &c->gpp, &c->stage, &c->h_P, &c->h_img, &c->h_sino, &c->h_total};
+                 &c->vtan, &c->Gpp, &c->gpp, &c->vtanP, &c->gq, &c->stage, &c->h_P, &c->h_img, &c->h_sino, &c->h_total};
   for (Buf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->d_status) cudaFree(c->d_status);
@@ -424,7 +453,7 @@ int ecc_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion,
   if (rc != ECC_OK) return rc;
   DeviceGuard g(c->device);
   return run_evaluate(c, n_views, P, motion, sino, scales, W, H, n_alpha, n_s, dtype, n_kappa, cauchy_c, pairs,
-                      n_pairs, total, per_pair, nkappa, nullptr, false, (cudaStream_t)stream);
+                      n_pairs, total, per_pair, nkappa, nullptr, nullptr, false, (cudaStream_t)stream);
 }
 
 int ecc_evaluate_frozen(ecc_ctx* c, int n_views, const double* P, const double* motion, const void* sino,
@@ -436,7 +465,7 @@ int ecc_evaluate_frozen(ecc_ctx* c, int n_views, const double* P, const double* 
   if (rc != ECC_OK) return rc;
   DeviceGuard g(c->device);
   return run_evaluate(c, n_views, P, motion, sino, scales, W, H, n_alpha, n_s, dtype, n_kappa, cauchy_c, pairs,
-                      n_pairs, total, per_pair, nkappa, nullptr, true, (cudaStream_t)stream);
+                      n_pairs, total, per_pair, nkappa, nullptr, nullptr, true, (cudaStream_t)stream);
 }
 
 int ecc_evaluate_grad(ecc_ctx* c, int n_views, const double* P, const double* motion, const void* sino,
@@ -449,7 +478,20 @@ int ecc_evaluate_grad(ecc_ctx* c, int n_views, const double* P, const double* mo
   if (!grad) return fail(c, ECC_EINVAL, "grad is NULL");
   DeviceGuard g(c->device);
   return run_evaluate(c, n_views, P, motion, sino, scales, W, H, n_alpha, n_s, dtype, n_kappa, cauchy_c, pairs,
-                      n_pairs, total, per_pair, nkappa, grad, false, (cudaStream_t)stream);
+                      n_pairs, total, per_pair, nkappa, grad, nullptr, false, (cudaStream_t)stream);
+}
+
+int ecc_evaluate_grad_projection(ecc_ctx* c, int n_views, const double* P, const double* motion, const void* sino,
+                                 const float* scales, int W, int H, int n_alpha, int n_s, int dtype, int n_kappa,
+                                 double cauchy_c, const int32_t* pairs, int n_pairs, double* total,
+                                 double* per_pair, int32_t* nkappa, double* grad_P, void* stream) {
+  int rc = check_eval_args(c, n_views, P, sino, scales, W, H, n_alpha, n_s, dtype, n_kappa, cauchy_c, pairs, n_pairs,
+                           total);
+  if (rc != ECC_OK) return rc;
+  if (!grad_P) return fail(c, ECC_EINVAL, "grad_P is NULL");
+  DeviceGuard g(c->device);
+  return run_evaluate(c, n_views, P, motion, sino, scales, W, H, n_alpha, n_s, dtype, n_kappa, cauchy_c, pairs,
+                      n_pairs, total, per_pair, nkappa, nullptr, grad_P, false, (cudaStream_t)stream);
 }
 
 int ecc_scan_consistency_host(ecc_ctx* c, int n_views, const double* P_host, const float* images_host, int W,
@@ -479,7 +521,8 @@ int ecc_scan_consistency_host(ecc_ctx* c, int n_views, const double* P_host, con
                       c->h_sino.p, nullptr, s);
   if (rc != ECC_OK) return rc;
   rc = run_evaluate(c, n_views, (const double*)c->h_P.p, nullptr, c->h_sino.p, nullptr, W, H, n_alpha, n_s, ECC_F32,
-                    n_kappa, cauchy_c, nullptr, (int)np, (double*)c->h_total.p, nullptr, nullptr, nullptr, false, s);
+                    n_kappa, cauchy_c, nullptr, (int)np, (double*)c->h_total.p, nullptr, nullptr, nullptr, nullptr, false,
+                    s);
   if (rc != ECC_OK) return rc;
   e = cudaMemcpyAsync(total_host, c->h_total.p, sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

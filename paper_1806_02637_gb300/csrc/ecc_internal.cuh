@@ -34,6 +34,12 @@ struct ViewTan {
   double dcofc[9][6];
 };
 
+// Tangents of the per-view quantities a pair reads, q = (C[3], up[3], cofc[9]), with
+// respect to the 12 entries of the view's (unmoved) projection matrix P.
+struct ViewTanP {
+  double d[15][12];
+};
+
 // Per-pair set-up (FP64 geometry, integer sample ranges).
 struct PairRec {
   double A[2][6];   // per view (a, b): l_centred(kappa) = A (cos kappa, sin kappa), 3x2 row-major

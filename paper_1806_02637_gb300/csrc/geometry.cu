@@ -32,8 +32,8 @@ template <int N>
 __device__ inline void sc_pair(const Dual<N>& x, Dual<N>* s, Dual<N>* c) { sincos(x, s, c); }
 
 // P T(theta), T = [R t; 0 1], R = Rz(rz) Ry(ry) Rx(rx).
-template <class T>
-__host__ __device__ void moved_projection(const double* P, const T* th, T* out) {
+template <class TP, class T>
+__host__ __device__ void moved_projection(const TP* P, const T* th, T* out) {
   T sx, cx, sy, cy, sz, cz;
   sc_pair(th[0], &sx, &cx);
   sc_pair(th[1], &sy, &cy);
@@ -42,7 +42,7 @@ __host__ __device__ void moved_projection(const double* P, const T* th, T* out) 
                   sz * cy, sz * sy * sx + cz * cx, sz * sy * cx - cz * sx,
                   -sy,     cy * sx,                cy * cx};
   for (int i = 0; i < 3; ++i) {
-    const double* p = P + 4 * i;
+    const TP* p = P + 4 * i;
     for (int j = 0; j < 3; ++j) out[4 * i + j] = p[0] * R[j] + p[1] * R[3 + j] + p[2] * R[6 + j];
     out[4 * i + 3] = p[0] * th[3] + p[1] * th[4] + p[2] * th[5] + T(p[3]);
   }
@@ -188,6 +188,34 @@ __global__ void view_tangent_kernel(int n_views, const double* __restrict__ P, c
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_views) return;
   out[i] = view_tangent(P + 12 * i, motion ? motion + 6 * i : nullptr, W, H);
+}
+
+// Tangents of q = (C, up, cofc) with respect to the 12 entries of the unmoved P
+// (forward mode, FP64; the view uses P T(theta)): one thread per (view, entry j),
+// one tangent direction each.
+__global__ void view_tangent_P_kernel(int n_views, const double* __restrict__ P, const double* __restrict__ motion,
+                                      int W, int H, ViewTanP* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 12LL * n_views) return;
+  const int lam = (int)(i / 12), j = (int)(i % 12);
+  using D1 = Dual<1>;
+  D1 Pd[12], Pm[12], Pn[12], C[3], up[3], cofc[9], u0, v0, D;
+  for (int k = 0; k < 12; ++k) Pd[k] = D1(P[12 * lam + k]);
+  Pd[j].d[0] = 1.0;
+  if (motion) {
+    D1 th[6];
+    for (int k = 0; k < 6; ++k) th[k] = D1(motion[6 * lam + k]);
+    moved_projection(Pd, th, Pm);
+  } else {
+    for (int k = 0; k < 12; ++k) Pm[k] = Pd[k];
+  }
+  view_geometry(Pm, W, H, Pn, C, up, cofc, &u0, &v0, &D);
+  ViewTanP& t = out[lam];
+  for (int k = 0; k < 3; ++k) {
+    t.d[k][j] = C[k].d[0];
+    t.d[3 + k][j] = up[k].d[0];
+  }
+  for (int k = 0; k < 9; ++k) t.d[6 + k][j] = cofc[k].d[0];
 }
 
 namespace {
@@ -438,6 +466,98 @@ __global__ void pair_grad_kernel(long long n_pairs, const PairRec* __restrict__ 
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n_pairs) return;
   pair_grad(prs[p], views, vtan, Gpp + 12 * p, gpp + 12 * p);
+}
+
+// Gradient of one pair's e with respect to the per-view quantities the pair reads,
+// q = (C[3], up[3], cofc[9]) of view a, then of view b (30 values): the frame
+// (w, v) carries forward-mode tangents in the sources and up axes (12
+// directions); A = cofc [w v] is linear in cofc.  G = d e / d A as for pair_grad.
+__device__ void pair_grad_q(const PairRec& pr, const ViewRec* __restrict__ views, const double* __restrict__ G,
+                            double* __restrict__ out) {
+  if (pr.status != 0 || pr.nk <= 0) {
+    for (int j = 0; j < 30; ++j) out[j] = 0.0;
+    return;
+  }
+  using D = Dual<12>;
+  const int ab[2] = {pr.a, pr.b};
+  D C[2][3], up[2][3];
+  for (int s = 0; s < 2; ++s) {
+    const ViewRec& vr = views[ab[s]];
+    for (int k = 0; k < 3; ++k) {
+      C[s][k] = D(vr.C[k]);
+      C[s][k].d[6 * s + k] = 1.0;
+      up[s][k] = D(vr.up[k]);
+      up[s][k].d[6 * s + 3 + k] = 1.0;
+    }
+  }
+  D w[3], v[3];
+  pencil_frame(C[0], C[1], up[0], up[1], w, v);
+  double gf[12];
+  for (int j = 0; j < 12; ++j) gf[j] = 0.0;
+  for (int s = 0; s < 2; ++s) {
+    const double* cof = views[ab[s]].cofc;
+    for (int i = 0; i < 3; ++i) {
+      const double g0 = G[6 * s + 2 * i], g1 = G[6 * s + 2 * i + 1];
+      for (int k = 0; k < 3; ++k) out[15 * s + 6 + 3 * i + k] = g0 * w[k].v + g1 * v[k].v;
+      for (int j = 0; j < 12; ++j)
+        gf[j] += g0 * (cof[3 * i] * w[0].d[j] + cof[3 * i + 1] * w[1].d[j] + cof[3 * i + 2] * w[2].d[j]) +
+                 g1 * (cof[3 * i] * v[0].d[j] + cof[3 * i + 1] * v[1].d[j] + cof[3 * i + 2] * v[2].d[j]);
+    }
+  }
+  for (int s = 0; s < 2; ++s)
+    for (int k = 0; k < 6; ++k) out[15 * s + k] = gf[6 * s + k];
+}
+
+__global__ void pair_grad_q_kernel(long long n_pairs, const PairRec* __restrict__ prs,
+                                   const ViewRec* __restrict__ views, const double* __restrict__ Gpp,
+                                   double* __restrict__ gq) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_pairs) return;
+  pair_grad_q(prs[p], views, Gpp + 12 * p, gq + 30 * p);
+}
+
+// Per-view sum of the pairs' q gradients in a fixed order (one block per view),
+// contracted with the view's tangents: grad_P[view][12] = sum_k dtotal/dq_k dq_k/dP.
+__global__ void __launch_bounds__(256) view_grad_P_kernel(int n_views, long long n_pairs,
+                                                          const int32_t* __restrict__ pairs,
+                                                          const double* __restrict__ gq,
+                                                          const ViewTanP* __restrict__ vtan,
+                                                          double* __restrict__ grad_P) {
+  __shared__ double sh[15][256];
+  const int lam = blockIdx.x;
+  double acc[15];
+  for (int k = 0; k < 15; ++k) acc[k] = 0.0;
+  if (pairs) {
+    for (long long p = threadIdx.x; p < n_pairs; p += blockDim.x) {
+      const int a = pairs[2 * p], b = pairs[2 * p + 1];
+      if (a == lam)
+        for (int k = 0; k < 15; ++k) acc[k] += gq[30 * p + k];
+      if (b == lam)
+        for (int k = 0; k < 15; ++k) acc[k] += gq[30 * p + 15 + k];
+    }
+  } else {
+    const long long n = n_views;
+    for (int o = threadIdx.x; o < n_views; o += blockDim.x) {
+      if (o == lam) continue;
+      const long long a = o < lam ? o : lam, b = o < lam ? lam : o;
+      const long long p = a * (2 * n - a - 1) / 2 + (b - a - 1);
+      const int off = o < lam ? 15 : 0;  // this view is b of the pair when o < lam
+      for (int k = 0; k < 15; ++k) acc[k] += gq[30 * p + off + k];
+    }
+  }
+  for (int k = 0; k < 15; ++k) sh[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int wdt = blockDim.x / 2; wdt > 0; wdt >>= 1) {
+    if (threadIdx.x < wdt)
+      for (int k = 0; k < 15; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + wdt];
+    __syncthreads();
+  }
+  if (threadIdx.x < 12) {
+    const ViewTanP& t = vtan[lam];
+    double g = 0.0;
+    for (int k = 0; k < 15; ++k) g += sh[k][0] * t.d[k][threadIdx.x];
+    grad_P[12 * lam + threadIdx.x] = g;
+  }
 }
 
 // Per-view sum of the pair gradients in a fixed order (one block per view):

@@ -17,6 +17,12 @@ __global__ void pair_grad_kernel(long long n_pairs, const PairRec* prs, const Vi
                                  const double* Gpp, double* gpp);
 __global__ void view_grad_reduce_kernel(int n_views, long long n_pairs, const int32_t* pairs, const double* gpp,
                                         double* grad);
+__global__ void view_tangent_P_kernel(int n_views, const double* P, const double* motion, int W, int H,
+                                      ViewTanP* out);
+__global__ void pair_grad_q_kernel(long long n_pairs, const PairRec* prs, const ViewRec* views, const double* Gpp,
+                                   double* gq);
+__global__ void view_grad_P_kernel(int n_views, long long n_pairs, const int32_t* pairs, const double* gq,
+                                   const ViewTanP* vtan, double* grad_P);
 __global__ void alpha_dir_kernel(int n_alpha, float4* dir);
 
 // Per (view, alpha-row) line parameters of the Joseph line sums (32.32 fixed point).

@@ -57,3 +57,15 @@ def sino_rel_err(S_gpu, S_ref):
     num = np.abs(S_gpu - S_ref).reshape(S_ref.shape[0], -1).max(axis=1)
     den = np.abs(S_ref).reshape(S_ref.shape[0], -1).max(axis=1)
     return num / den
+
+
+def p_entry_scale(P):
+    """Per-entry scale of projection matrices [n, 12]: the largest |M| entry of the
+    row for the first three columns, |t| plus 100 times that for the last (a
+    distance in mm times the row's scale).  Used to compare and step gradients with
+    respect to P in units of relative change of each entry."""
+    P = np.asarray(P, dtype=np.float64).reshape(-1, 3, 4)
+    s = np.empty_like(P)
+    s[:, :, :3] = np.abs(P[:, :, :3]).max(axis=2, keepdims=True)
+    s[:, :, 3] = np.abs(P[:, :, 3]) + 100.0 * s[:, :, 0]
+    return s.reshape(-1, 12)

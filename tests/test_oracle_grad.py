@@ -7,6 +7,7 @@ import numpy as np
 
 import synth
 from oracle import oracle as orc
+from tests import helpers as H
 
 K = 96
 
@@ -65,16 +66,6 @@ def test_grad_global_rigid_null_space():
 # ------------------------------------------------ gradient w.r.t. the entries of P
 # (geometric calibration by the consistency, Introduction): the view uses P T(theta)
 
-def _rel_steps(P, eps):
-    """Per-entry steps relative to the entry's row (entries of one row of P share a
-    scale; the last column is larger by a distance in mm)."""
-    P = P.reshape(-1, 3, 4)
-    sc = np.empty_like(P)
-    sc[:, :, :3] = np.abs(P[:, :, :3]).max(axis=2, keepdims=True)
-    sc[:, :, 3] = np.abs(P[:, :, 3]) + 100.0 * sc[:, :, 0]
-    return (eps * sc).reshape(-1, 12)
-
-
 def test_grad_P_vs_central_differences():
     cfg, sc, S = _scan()
     nv = len(sc["P"])
@@ -85,7 +76,7 @@ def test_grad_P_vs_central_differences():
     rng = np.random.default_rng(33)
     picks = rng.choice(nv * 12, size=32, replace=False)
     for eps, tol in ((1e-6, 0.35), (1e-8, 3e-3), (1e-9, 5e-4)):
-        steps = _rel_steps(sc["P"], eps)
+        steps = eps * H.p_entry_scale(sc["P"])
         fd, an = [], []
         for q in picks:
             h = steps.flat[q]
