@@ -67,17 +67,17 @@ constexpr int kSer = 10;           // terms of the per-tile series
 constexpr float kSerLimit = 0.1f;  // series used while |zeta| tan(15.5 dk) <= this
 
 // Per (tile, view) anchor record, 32 floats (128 B), written by one lane and read by
-// the whole warp through shared memory.
+// the whole warp through shared memory.  The fields of the series path come first.
 struct Anchor {
   int m0, n0;      // alpha row and s bin of the tile-centre line
   float fa0, fs0;  // fractional parts (may leave [0,1) slightly)
-  float a, b;      // zeta = a + i b: rate of the normal direction in the anchor frame
-  float p3, s0;    // rate of the offset, anchor offset s [px]
   float sg;        // orientation fold of the anchor (+1 / -1)
   float gh, gl;    // exact s-index advance per sample step: gh (17 significant bits) + gl
-  float ser;       // 1: the series below holds over this tile, 0: closed form per sample
-  float dco[kSer];  // alpha offset [bins] = sum_k dco[k-1] t^k,  t = tan(delta)
-  float sco[kSer];  // s remainder [bins] = sco[0] (t - delta) + sum_{k>=2} sco[k-1] t^k
+  float ser;       // number of series terms that hold over this tile (2 .. kSer), 0: closed form per sample
+  float dco[kSer];  // alpha offset [bins] = sum_k dco[k-1] t^k,  t = tan(delta); zero beyond ser terms
+  float sco[kSer];  // s remainder [bins] = sco[0] (t - delta) + sum_{k>=2} sco[k-1] t^k; zero beyond ser
+  float a, b;      // zeta = a + i b: rate of the normal direction in the anchor frame
+  float p3, s0;    // rate of the offset, anchor offset s [px]
 };
 static_assert(sizeof(Anchor) == 128, "anchor record is 32 floats");
 
@@ -141,18 +141,31 @@ __device__ Anchor make_anchor(const float* __restrict__ Adf, float4 c, const flo
   const df ux = {u.x, u.z}, uy = {u.y, u.w};
   const df cr = df_sub(df_mul(ux, l1), df_mul(uy, l0));  // h sin(alpha - alpha_m)
   const df dt = df_add(df_mul(ux, l0), df_mul(uy, l1));  // h cos(alpha - alpha_m)
-  const float th = atan2f(cr.hi, dt.hi);
+  // turn th from the row direction: within about one alpha bin, so atan, sin(th/2)
+  // and cos(th) = 1 - 2 sin^2(th/2) come from short odd/even series (truncation below
+  // 1e-12 relative for |th| <= 0.05); wider turns (coarse alpha grids) use the library
+  const float xr = cr.hi / dt.hi;
+  float th, sh;
+  if (fabsf(xr) <= 0.05f && dt.hi > 0.0f) {
+    const float x2 = xr * xr;
+    th = xr * fmaf(x2, fmaf(x2, fmaf(x2, -1.0f / 7.0f, 1.0f / 5.0f), -1.0f / 3.0f), 1.0f);
+    const float y = 0.5f * th, y2 = y * y;
+    sh = y * fmaf(y2, fmaf(y2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f);
+  } else {
+    th = atan2f(cr.hi, dt.hi);
+    sh = sinf(0.5f * th);
+  }
   r.m0 = m;
   r.fa0 = th * inv_dalpha;
   // s = -l2 / h = (-l2 / dt) cos(th)
   const df sigma = df_neg(df_mul(l2, df_recip(dt)));
   float frac;
   const float nf = df_floor_frac(df_add(df_mul(sigma, inv_ds), half_ns1), &frac);
-  const float sh = sinf(0.5f * th);
   const float sigf = sigma.hi;
-  r.n0 = (int)nf;
-  r.fs0 = frac - sigf * 2.0f * sh * sh * inv_ds_f;
-  r.s0 = sigf * cosf(th);
+  const float vers = 2.0f * sh * sh;  // 1 - cos(th)
+  r.n0 = (int)fminf(fmaxf(nf, -4.0e6f), 4.0e6f);  // a masked tile centre may lie far outside
+  r.fs0 = frac - sigf * vers * inv_ds_f;
+  r.s0 = sigf * (1.0f - vers);
   // exact first-order advance of the s index per sample: (ds/dkappa) dk / ds_bin,
   // ds/dkappa = (1/h) (-l2' + l2 (l . l') / h^2)
   const df ih = df_rsqrt(df_add(df_mul(l0, l0), df_mul(l1, l1)));
@@ -170,11 +183,31 @@ __device__ Anchor make_anchor(const float* __restrict__ Adf, float4 c, const flo
   // With |zeta t| <= 0.1 the truncation after t^10 is below 1e-10 of the offsets.
   const float zr = r.a, zi = r.b;
   const float z2 = fmaf(zr, zr, zi * zi);
-  r.ser = sqrtf(z2) * tan_half_tile <= kSerLimit ? 1.0f : 0.0f;
+  // Terms needed: with rho = |zeta| tan(half tile) the k-th terms are bounded by
+  // rho^k inv_dalpha (alpha) and (|s0| rho^k + |p3| t rho^(k-1)) inv_ds (s), since
+  // |Im zeta^k| <= |zeta|^k and |e_k| <= |zeta|^k; the tails after n terms are these
+  // geometric sums.  The smallest n >= 2 whose tail bound is below 1e-8 bins is kept
+  // (the s index carries ~6e-8 bins of FP32 rounding anyway).
+  const float rho = sqrtf(z2) * tan_half_tile;
+  int nser = 0;
+  if (rho <= kSerLimit && isfinite(r.s0) && isfinite(r.fs0) && isfinite(r.fa0)) {
+    const float cs = fabsf(r.s0) * inv_ds_f, cp = fabsf(r.p3) * tan_half_tile * inv_ds_f;
+    const float inv1m = 1.0f / (1.0f - rho);
+    float rn = rho * rho;  // rho^n for n = 2
+    nser = 2;
+    while (nser < kSer && ((inv_dalpha + cs) * rn * rho + cp * rn) * inv1m > 1e-8f) {
+      rn *= rho;
+      ++nser;
+    }
+  }
+  r.ser = (float)nser;
+#pragma unroll
+  for (int k = 0; k < kSer; ++k) r.dco[k] = r.sco[k] = 0.0f;
   float pre = zr, pim = zi;        // zeta^k
   float e_prev = 1.0f, e_cur = -zr;  // e_(k-1), e_k
 #pragma unroll
   for (int k = 1; k <= kSer; ++k) {
+    if (k > nser) break;
     r.dco[k - 1] = ((k & 1) ? pim : -pim) * inv_dalpha * (1.0f / (float)k);
     r.sco[k - 1] = fmaf(r.s0, e_cur, -r.p3 * e_prev) * inv_ds_f;
     const float e_next = -fmaf((float)(2 * k + 1) * zr, e_cur, (float)k * z2 * e_prev) * (1.0f / (float)(k + 1));
@@ -334,6 +367,248 @@ __device__ __forceinline__ float sample_grad(const T* __restrict__ sv, int n_alp
   return scale * sign * fmaf(fa, v1 - v0, v0);
 }
 
+// ------------------------------------------------------------ forward fast path
+//
+// The forward kernel evaluates a tile with the anchors' own number of series terms
+// (warp-uniform), without per-sample clamps and with two-row gathers at 32-bit
+// indices.  A tile in which some lane's alpha row is outside [0, n_alpha - 2] (the
+// fold at alpha = pi and the wrap of the last row) or in which a view needs the
+// closed form is evaluated by the general per-sample code above instead.  Positions
+// are bitwise those of the general code (zero coefficients beyond the anchor's
+// terms leave its Horner chains unchanged).
+
+// Per-lane constants of one tile shape (full tiles, or the ragged last tile).
+struct LaneGeom {
+  float jj, de, t, t2, tmd, cd, sd;
+};
+
+template <int NT>
+__device__ __forceinline__ void series_position(const float4* __restrict__ rec, const LaneGeom& q, unsigned& mu,
+                                                int& n, float& fa, float& fs) {
+  const float4 h0 = rec[0], h1 = rec[1];
+  const float* __restrict__ c = reinterpret_cast<const float*>(rec + 2);  // dco[kSer], sco[kSer]
+  float da = c[NT - 1];
+#pragma unroll
+  for (int k = NT - 2; k >= 0; --k) da = fmaf(da, q.t, c[k]);
+  da *= q.t;
+  float sr = c[kSer + NT - 1];
+#pragma unroll
+  for (int k = NT - 2; k >= 1; --k) sr = fmaf(sr, q.t, c[kSer + k]);
+  sr = fmaf(c[kSer], q.tmd, q.t2 * sr);
+  const float lin = h1.y * q.jj;  // gh * jj: exact
+  const float Li = floorf(lin);
+  const float fa_ = h0.z + da;
+  const float fs_ = (h0.w + (lin - Li)) + fmaf(h1.z, q.jj, sr);
+  const float mf = floorf(fa_), nf = floorf(fs_);
+  // unsigned sums: a masked lane may carry any value; its row is rejected below
+  mu = (unsigned)__float_as_int(h0.x) + (unsigned)(int)mf;
+  n = (int)((unsigned)__float_as_int(h0.y) + (unsigned)(int)(Li + nf));
+  fa = fa_ - mf;
+  fs = fs_ - nf;
+}
+
+// Bilinear value at row m (0 <= m <= n_alpha - 2) and bin n (clamped to [0, n_s - 2]);
+// n_alpha n_s < 2^32, so the element index fits 32 bits.
+template <typename T>
+__device__ __forceinline__ float bilinear_rows(const T* __restrict__ sv, int n_s, unsigned m, int n, float fa,
+                                               float fs) {
+  n = min(max(n, 0), n_s - 2);
+  const unsigned i0 = m * (unsigned)n_s + (unsigned)n;
+  const T* __restrict__ r0 = sv + i0;
+  const T* __restrict__ r1 = sv + (i0 + (unsigned)n_s);
+  const float t00 = Elem<T>::get(r0), t01 = Elem<T>::get(r0 + 1);
+  const float t10 = Elem<T>::get(r1), t11 = Elem<T>::get(r1 + 1);
+  const float v0 = fmaf(fs, t01 - t00, t00);
+  const float v1 = fmaf(fs, t11 - t10, t10);
+  return fmaf(fa, v1 - v0, v0);
+}
+
+// Difference S_a - S_b of this lane's sample by the general per-sample code.
+template <typename T>
+__device__ __noinline__ float tile_diff_general(const float4* __restrict__ ra, const float4* __restrict__ rb,
+                                               const LaneGeom& q, const T* __restrict__ sa,
+                                               const T* __restrict__ sb, float sca, float scb, int n_alpha,
+                                               int n_s, float inv_dalpha, float inv_ds_f) {
+  Loc la, lb;
+  {
+    const Anchor an = load_anchor(ra);
+    la = an.ser != 0.0f ? locate_series(an, q.t, q.tmd, q.jj, n_alpha, n_s)
+                        : locate(an, q.cd, q.sd, q.jj, q.de, n_alpha, n_s, inv_dalpha, inv_ds_f);
+  }
+  {
+    const Anchor an = load_anchor(rb);
+    lb = an.ser != 0.0f ? locate_series(an, q.t, q.tmd, q.jj, n_alpha, n_s)
+                        : locate(an, q.cd, q.sd, q.jj, q.de, n_alpha, n_s, inv_dalpha, inv_ds_f);
+  }
+  return sca * sample(sa, n_alpha, n_s, la) - scb * sample(sb, n_alpha, n_s, lb);
+}
+
+template <typename T, int NT>
+__device__ __forceinline__ float tile_diff_series(const float4* __restrict__ ra, const float4* __restrict__ rb,
+                                                 const LaneGeom& q, const T* __restrict__ sa,
+                                                 const T* __restrict__ sb, float sca, float scb, int n_alpha,
+                                                 int n_s, float inv_dalpha, float inv_ds_f) {
+  unsigned ma, mb;
+  int na, nb;
+  float faa, fsa, fab, fsb;
+  series_position<NT>(ra, q, ma, na, faa, fsa);
+  series_position<NT>(rb, q, mb, nb, fab, fsb);
+  const unsigned last = (unsigned)(n_alpha - 1);
+  if (__any_sync(0xffffffffu, ma >= last || mb >= last))  // fold or last-row wrap somewhere in the tile
+    return tile_diff_general<T>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f);
+  const float ga = sca * ra[1].x, gb = scb * rb[1].x;  // storage scale times the anchor's fold
+  return ga * bilinear_rows(sa, n_s, ma, na, faa, fsa) - gb * bilinear_rows(sb, n_s, mb, nb, fab, fsb);
+}
+
+// Two consecutive full tiles at once (twice the gathers in flight per warp).
+template <typename T, int NT>
+__device__ __forceinline__ bool tile_diff2_series(const float4* __restrict__ ra0, const float4* __restrict__ rb0,
+                                                  const float4* __restrict__ ra1, const float4* __restrict__ rb1,
+                                                  const LaneGeom& q, const T* __restrict__ sa,
+                                                  const T* __restrict__ sb, float sca, float scb, int n_alpha,
+                                                  int n_s, float& d0, float& d1) {
+  unsigned ma0, mb0, ma1, mb1;
+  int na0, nb0, na1, nb1;
+  float fa0, fs0, fb0, gs0, fa1, fs1, fb1, gs1;
+  series_position<NT>(ra0, q, ma0, na0, fa0, fs0);
+  series_position<NT>(rb0, q, mb0, nb0, fb0, gs0);
+  series_position<NT>(ra1, q, ma1, na1, fa1, fs1);
+  series_position<NT>(rb1, q, mb1, nb1, fb1, gs1);
+  const unsigned last = (unsigned)(n_alpha - 1);
+  if (__any_sync(0xffffffffu, ma0 >= last || mb0 >= last || ma1 >= last || mb1 >= last)) return false;
+  const float ga0 = sca * ra0[1].x, gb0 = scb * rb0[1].x, ga1 = sca * ra1[1].x, gb1 = scb * rb1[1].x;
+  const float A0 = bilinear_rows(sa, n_s, ma0, na0, fa0, fs0), B0 = bilinear_rows(sb, n_s, mb0, nb0, fb0, gs0);
+  const float A1 = bilinear_rows(sa, n_s, ma1, na1, fa1, fs1), B1 = bilinear_rows(sb, n_s, mb1, nb1, fb1, gs1);
+  d0 = ga0 * A0 - gb0 * B0;
+  d1 = ga1 * A1 - gb1 * B1;
+  return true;
+}
+
+template <typename T>
+__device__ __forceinline__ bool tile_diff2(const float4* __restrict__ ra0, const float4* __restrict__ rb0,
+                                           const float4* __restrict__ ra1, const float4* __restrict__ rb1,
+                                           const LaneGeom& q, const T* __restrict__ sa, const T* __restrict__ sb,
+                                           float sca, float scb, int n_alpha, int n_s, float& d0, float& d1) {
+  const float n0 = fminf(fminf(ra0[1].w, rb0[1].w), fminf(ra1[1].w, rb1[1].w));
+  if (n0 == 0.0f) return false;
+  const float nt = fmaxf(fmaxf(ra0[1].w, rb0[1].w), fmaxf(ra1[1].w, rb1[1].w));
+  if (nt <= 3.0f) return tile_diff2_series<T, 3>(ra0, rb0, ra1, rb1, q, sa, sb, sca, scb, n_alpha, n_s, d0, d1);
+  if (nt <= 4.0f) return tile_diff2_series<T, 4>(ra0, rb0, ra1, rb1, q, sa, sb, sca, scb, n_alpha, n_s, d0, d1);
+  if (nt <= 6.0f) return tile_diff2_series<T, 6>(ra0, rb0, ra1, rb1, q, sa, sb, sca, scb, n_alpha, n_s, d0, d1);
+  if (nt <= 8.0f) return tile_diff2_series<T, 8>(ra0, rb0, ra1, rb1, q, sa, sb, sca, scb, n_alpha, n_s, d0, d1);
+  return tile_diff2_series<T, kSer>(ra0, rb0, ra1, rb1, q, sa, sb, sca, scb, n_alpha, n_s, d0, d1);
+}
+
+template <typename T>
+__device__ __forceinline__ float tile_diff(const float4* __restrict__ ra, const float4* __restrict__ rb,
+                                          const LaneGeom& q, const T* __restrict__ sa, const T* __restrict__ sb,
+                                          float sca, float scb, int n_alpha, int n_s, float inv_dalpha,
+                                          float inv_ds_f) {
+  const float na = ra[1].w, nb = rb[1].w;  // terms of the two anchors (warp-uniform)
+  if (na == 0.0f || nb == 0.0f)
+    return tile_diff_general<T>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f);
+  const float nt = fmaxf(na, nb);
+  if (nt <= 3.0f) return tile_diff_series<T, 3>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f);
+  if (nt <= 4.0f) return tile_diff_series<T, 4>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f);
+  if (nt <= 6.0f) return tile_diff_series<T, 6>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f);
+  if (nt <= 8.0f) return tile_diff_series<T, 8>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f);
+  return tile_diff_series<T, kSer>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f);
+}
+
+// Forward value of pair p on one warp: d, e and N_kappa (as pair_warp<T, false>).
+template <typename T>
+__device__ __forceinline__ double pair_warp_forward(const PairArgs& g, long long p, int lane,
+                                                    float4* __restrict__ recw) {
+  const PairRec& pr = g.prs[p];
+  const int nk = pr.status == 0 ? pr.nk : 0;
+  const int n_tiles = g.n_tiles, n_alpha = g.n_alpha, n_s = g.n_s, K = g.K;
+  float acc = 0.0f;
+  if (nk > 0) {
+    const T* __restrict__ sino = static_cast<const T*>(g.sino);
+    const size_t vstride = (size_t)n_alpha * n_s;
+    const T* __restrict__ sa = sino + (size_t)pr.a * vstride;
+    const T* __restrict__ sb = sino + (size_t)pr.b * vstride;
+    const float sca = g.scales ? g.scales[pr.a] : 1.0f;
+    const float scb = g.scales ? g.scales[pr.b] : 1.0f;
+    const float inv_dalpha = g.inv_dalpha, inv_ds_f = g.inv_ds_f;
+    const df inv_ds = {g.inv_ds_hi, g.inv_ds_lo};
+    const df half_ns1 = {g.half_hi, g.half_lo};
+    const float dkf = pr.dk_hi;
+    const df dk = {pr.dk_hi, pr.dk_lo};
+    auto lane_geom = [&](float jj) {
+      LaneGeom q;
+      q.jj = jj;
+      q.de = jj * dkf;
+      sincosf(q.de, &q.sd, &q.cd);
+      q.t = tanf(q.de);
+      q.t2 = q.t * q.t;
+      q.tmd = tan_minus_angle(q.de, q.t);
+      return q;
+    };
+    const int n_last = K - 32 * (n_tiles - 1);  // samples of the last tile (1 .. 32)
+    const LaneGeom qf = lane_geom((float)lane - 15.5f);
+    const LaneGeom ql = lane_geom((float)lane + 0.5f - 0.5f * (float)n_last);
+    const float tan_half_tile = tanf(15.5f * dkf);
+    const int r0lo = pr.r0lo, r1lo = pr.r1lo;
+    const unsigned len0 = (unsigned)max(pr.r0hi - pr.r0lo, 0), len1 = (unsigned)max(pr.r1hi - pr.r1lo, 0);
+    const float4* __restrict__ ct = g.ctile + p * n_tiles;
+    for (int t0 = 0; t0 < n_tiles; t0 += 16) {
+      {
+        const int v = lane >> 4;
+        int t = t0 + (lane & 15);
+        if (t >= n_tiles) t = n_tiles - 1;
+        store_anchor(recw + 8 * lane, make_anchor(pr.Af[v], ct[t], g.alpha_dir, n_alpha, inv_dalpha, inv_ds,
+                                                  half_ns1, inv_ds_f, dk, tan_half_tile));
+      }
+      __syncwarp();
+      const int tmax = min(16, n_tiles - t0);
+      const int tfull = (t0 + tmax == n_tiles && n_last != 32) ? tmax - 1 : tmax;
+      int tt = 0;
+      for (; tt + 1 < tfull; tt += 2) {
+        const int k = 32 * (t0 + tt) + lane;
+        const bool v0 = (unsigned)(k - r0lo) < len0 || (unsigned)(k - r1lo) < len1;
+        const bool v1 = (unsigned)(k + 32 - r0lo) < len0 || (unsigned)(k + 32 - r1lo) < len1;
+        float d0, d1;
+        if (!tile_diff2<T>(recw + 8 * tt, recw + 8 * (16 + tt), recw + 8 * (tt + 1), recw + 8 * (17 + tt), qf, sa,
+                           sb, sca, scb, n_alpha, n_s, d0, d1)) {
+          d0 = tile_diff<T>(recw + 8 * tt, recw + 8 * (16 + tt), qf, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha,
+                            inv_ds_f);
+          d1 = tile_diff<T>(recw + 8 * (tt + 1), recw + 8 * (17 + tt), qf, sa, sb, sca, scb, n_alpha, n_s,
+                            inv_dalpha, inv_ds_f);
+        }
+        acc += v0 ? d0 * d0 : 0.0f;
+        acc += v1 ? d1 * d1 : 0.0f;
+      }
+      for (; tt < tfull; ++tt) {
+        const int k = 32 * (t0 + tt) + lane;
+        const bool valid = (unsigned)(k - r0lo) < len0 || (unsigned)(k - r1lo) < len1;
+        const float dd = tile_diff<T>(recw + 8 * tt, recw + 8 * (16 + tt), qf, sa, sb, sca, scb, n_alpha, n_s,
+                                      inv_dalpha, inv_ds_f);
+        acc += valid ? dd * dd : 0.0f;
+      }
+      if (tfull < tmax) {  // the ragged last tile
+        const int k = 32 * (t0 + tfull) + lane;
+        const bool valid = k < K && ((unsigned)(k - r0lo) < len0 || (unsigned)(k - r1lo) < len1);
+        const float dd = tile_diff<T>(recw + 8 * tfull, recw + 8 * (16 + tfull), ql, sa, sb, sca, scb, n_alpha,
+                                      n_s, inv_dalpha, inv_ds_f);
+        acc += valid ? dd * dd : 0.0f;
+      }
+      __syncwarp();  // records are rewritten by the next chunk
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  const float d = nk > 0 ? acc / (float)nk : 0.0f;
+  const float e = g.cauchy_c > 0.0f ? d / (1.0f + d / g.cauchy_c) : d;
+  if (lane == 0) {
+    if (g.per_pair) {
+      g.per_pair[2 * p] = (double)d;
+      g.per_pair[2 * p + 1] = (double)e;
+    }
+    if (g.nk_out) g.nk_out[p] = nk;
+  }
+  return (double)e;
+}
+
 // One pair per warp (one plane per lane, tiles of 32): d, e and N_kappa of pair p
 // and, for GRAD, the adjoint d e / d A; returns e on every lane.  Inlined into the
 // single-scan kernel and the serving kernel; the two compiled copies may round
@@ -482,8 +757,11 @@ template <typename T, bool GRAD>
 __device__ __forceinline__ void pair_block(const PairArgs& g, long long blk, double* e_warp, float4* recs) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long p = blk * kWarpsPerBlock + wib;
-  const double e_val =
-      p < g.n_pairs ? pair_warp<T, GRAD>(g, p, lane, recs + (size_t)wib * 32 * 8) : 0.0;  // warp-uniform
+  double e_val = 0.0;
+  if (p < g.n_pairs) {  // warp-uniform
+    float4* recw = recs + (size_t)wib * 32 * 8;
+    e_val = GRAD ? pair_warp<T, true>(g, p, lane, recw) : pair_warp_forward<T>(g, p, lane, recw);
+  }
   if (lane == 0) e_warp[wib] = e_val;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -494,8 +772,10 @@ __device__ __forceinline__ void pair_block(const PairArgs& g, long long blk, dou
   __syncthreads();
 }
 
+// The forward kernel runs four blocks per SM (64 registers: more gathers in flight);
+// the adjoint keeps three (its per-sample state is larger).
 template <typename T, bool GRAD>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 3) ecc_pair_kernel(PairArgs g) {
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, GRAD ? 3 : 4) ecc_pair_kernel(PairArgs g) {
   __shared__ double e_warp[kWarpsPerBlock];
   __shared__ float4 recs[kWarpsPerBlock * 32 * 8];  // anchor records, 4 KB per warp
   pair_block<T, GRAD>(g, blockIdx.x, e_warp, recs);
