@@ -153,7 +153,7 @@ struct JosephArgs {
 
 // Taps of rows u in [ua, ub) of one anchor block (all 16 rows when FULL).
 template <bool CLAMP, bool FULL>
-__device__ __forceinline__ void joseph_block(uint64_t rp, float f0, float dyf, float lo_c, float hi_c,
+__device__ __forceinline__ void joseph_block(const float2* __restrict__ rp, float f0, float dyf, float lo_c, float hi_c,
                                              const float (&Mu)[kRowsPerAnchor], int ua, int ub, float& acc,
                                              float& comp) {
 #pragma unroll
@@ -167,7 +167,7 @@ __device__ __forceinline__ void joseph_block(uint64_t rp, float f0, float dyf, f
         if (CLAMP) xf = fminf(fmaxf(xf, lo_c), hi_c);
         const float t = __fadd_rd(xf, Mu[u]);
         const float f = xf - (t - Mu[u]);
-        const float2 vd = __ldg(reinterpret_cast<const float2*>(rp + 8ull * __float_as_uint(t)));
+        const float2 vd = __ldg(rp + __float_as_uint(t));
         s += fmaf(f, vd.y, vd.x);
       }
     }
@@ -225,11 +225,13 @@ __global__ void __launch_bounds__(32 * kAlphaPerBlock) joseph_kernel(const Radon
   for (int u = 0; u < kRowsPerAnchor; ++u) Mu[u] = kMagic + (float)(u * pitch);
   long long X = row.B0 + (long long)k * row.STEP + (long long)s_lo * row.DY;
   float acc = 0.0f, comp = 0.0f;
+  // row pointers are biased by -kMagicBits elements, so that a tap's element is the
+  // pointer plus the bit pattern of its round-down sum (one 32x32+64 multiply-add)
   const uint64_t img_b = reinterpret_cast<uint64_t>(img) - 8ull * kMagicBits;
   for (int j0 = s_lo; j0 < s_hi; j0 += kRowsPerAnchor) {
     const int xi0 = (int)(X >> 32);
     const float f0 = __uint_as_float(0x3f800000u | ((unsigned)X >> 9)) - 1.0f;
-    const uint64_t rp = img_b + 8ull * (uint64_t)((long long)j0 * pitch + g.pad + xi0);
+    const float2* rp = reinterpret_cast<const float2*>(img_b + 8ull * (uint64_t)((long long)j0 * pitch + g.pad + xi0));
     const float lo_c = (float)(-2 - xi0), hi_c = (float)(limit - xi0);
     const int n = s_hi - j0;
     if (n >= kRowsPerAnchor)
