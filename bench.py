@@ -433,9 +433,9 @@ def run_ours(args):
         flops = FLOPS_PER_TAP * taps * args.steps / n_dom
         achieved = flops / (ms_dom / n_dom / 1e3) / 1e12
         # DRAM bytes (read + write) of one launch, from an ncu capture of a 32-view launch of this
-        # kernel (183.7 MB + 58.7 MB), scaled to the views of an average launch of this step
+        # kernel (183.3 MB + 58.3 MB), scaled to the views of an average launch of this step
         views_per_launch = cfg.n_views * args.steps / n_dom
-        traffic = (183.679744e6 + 58.748160e6) / 32 * views_per_launch
+        traffic = (183.299840e6 + 58.299392e6) / 32 * views_per_launch
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a 32-view launch, "
