@@ -11,7 +11,10 @@ is one (pair, kappa) sample with both look-ups.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  Under torchrun with N > 1 every rank runs its own
-independent copy of the workload (weak scaling; no data-path collective).
+independent copy of the workload (weak scaling; no data-path collective).  Besides
+the contract's keys the line carries the per-kernel shares, the evaluation alone
+(FP32 storage), the same evaluation on FP16 and BF16 sinograms against the FP32
+total ("storage_forms"), and the served form with p50/p99 latency ("serving").
 """
 from __future__ import annotations
 
@@ -48,6 +51,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving (continuous batching) leg")
+    ap.add_argument("--no-storage-forms", action="store_true",
+                    help="skip the FP16/BF16 sinogram storage leg (evaluation against the FP32 form)")
     ap.add_argument("--serve-jobs", type=int, default=24, help="jobs of the serving leg")
     ap.add_argument("--serve-rate", type=float, default=20.0, help="mean Poisson arrival rate [jobs/s]")
     ap.add_argument("--views", type=int, default=0,
@@ -332,6 +337,45 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ storage forms
+def storage_forms(ctx, P, images, cfg, total_f32, reps=10):
+    """The reduced-precision form: the same scan's sinograms stored in FP16 (per-view
+    scale) and BF16, then the evaluation of all pairs timed as in the FP32 form (the
+    library's CUDA events, inputs resident).  Reports line-pair samples/s of the
+    evaluation, the pair kernel against HBM at 16 B per line pair, and the total's
+    relative difference from the plain FP32 form on the same GPU."""
+    import torch
+    import paper_1806_02637_gb300 as ecc
+    units = cfg.n_pairs * cfg.K
+    peaks = measured_peaks()
+    out = {}
+    for name, dt in (("float16", torch.float16), ("bfloat16", torch.bfloat16)):
+        S, scales = ecc.ecc_precompute_radon_derivative(ctx, P, images, cfg.n_alpha, cfg.n_s, dtype=dt)
+        tot = torch.empty((1,), dtype=torch.float64, device=S.device)
+        for _ in range(3):
+            ecc.ecc_evaluate(ctx, P, S, cfg.W, cfg.H, cfg.K, scales=scales, total=tot, want_per_pair=False)
+        torch.cuda.synchronize()
+        ecc.ecc_profile_read(ctx)
+        ecc.ecc_profile_enable(ctx, True)
+        for _ in range(reps):
+            ecc.ecc_evaluate(ctx, P, S, cfg.W, cfg.H, cfg.K, scales=scales, total=tot, want_per_pair=False)
+        torch.cuda.synchronize()
+        prof = ecc.ecc_profile_read(ctx)
+        ecc.ecc_profile_enable(ctx, False)
+        eval_ms = sum(prof[n][1] for n in ("alpha_dir_kernel", "pair_setup_kernel", "ecc_pair_kernel",
+                                           "reduce_kernel") if n in prof) / reps
+        pk_ms = prof["ecc_pair_kernel"][1] / prof["ecc_pair_kernel"][0]
+        gbs = 16.0 * units / (pk_ms / 1e3) / 1e9
+        t = float(tot.cpu()[0])
+        out[name] = {"ms_per_eval": eval_ms, "line_pairs_per_s": units / (eval_ms / 1e3), "pair_kernel_ms": pk_ms,
+                     "pair_kernel_gather_gbs": gbs, "pair_kernel_frac_of_hbm": gbs / peaks.get("hbm_gbs", 6800.0),
+                     "total": t, "total_rel_diff_vs_f32": abs(t - total_f32) / abs(total_f32)}
+        del S, scales
+    out["note"] = ("evaluation only (view/pair set-up, pair kernel, reduction), 16 B per line pair for the gather; "
+                   "the sinograms come from the same precompute in the stated storage type")
+    return out
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
@@ -468,6 +512,9 @@ def run_ours(args):
                      "pair_kernel_ms": pk["ms_per_step"],
                      "pair_kernel_gather_gbs": gbs,
                      "pair_kernel_frac_of_hbm": gbs / peaks.get("hbm_gbs", 6800.0)}
+    forms = None
+    if not args.no_storage_forms:
+        forms = storage_forms(ctx, P, images, cfg, result_total)
     serving = None
     if not args.no_serving and world == 1:
         serving = serving_leg(args, scan)
@@ -483,7 +530,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(cfg),
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
-            "kernels": kern, "ecc_eval_only": eval_only, "serving": serving, "total": result_total,
+            "kernels": kern, "ecc_eval_only": eval_only, "storage_forms": forms, "serving": serving,
+            "total": result_total,
             "geometry_precision": "f64 per-view/per-pair set-up, double-float (~48-bit) tile anchors, f32 per-sample"}
     print(json.dumps(line), flush=True)
     return 0
