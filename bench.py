@@ -14,7 +14,8 @@ Prints one JSON line (rank 0).  Under torchrun with N > 1 every rank runs its ow
 independent copy of the workload (weak scaling; no data-path collective).  Besides
 the contract's keys the line carries the per-kernel shares, the evaluation alone
 (FP32 storage), the same evaluation on FP16 and BF16 sinograms against the FP32
-total ("storage_forms"), and the served form with p50/p99 latency ("serving").
+total ("storage_forms"), the motion and calibration gradients on the same
+sinograms ("adjoint_forms"), and the served form with p50/p99 latency ("serving").
 """
 from __future__ import annotations
 
@@ -51,6 +52,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving (continuous batching) leg")
+    ap.add_argument("--no-adjoint-forms", action="store_true",
+                    help="skip the gradient legs (motion gradient and calibration gradient on the same sinograms)")
     ap.add_argument("--no-storage-forms", action="store_true",
                     help="skip the FP16/BF16 sinogram storage leg (evaluation against the FP32 form)")
     ap.add_argument("--serve-jobs", type=int, default=24, help="jobs of the serving leg")
@@ -376,6 +379,41 @@ def storage_forms(ctx, P, images, cfg, total_f32, reps=10):
     return out
 
 
+# ------------------------------------------------------------------ adjoint forms
+def adjoint_forms(ctx, P, sino, cfg, reps=5):
+    """The differentiated forms on the same FP32 sinograms, with a seeded rigid motion
+    (rotations N(0, 1 deg), translations N(0, 2 mm)): ecc_evaluate_grad (d total / d theta,
+    6 per view) and ecc_evaluate_grad_projection (d total / d P, 12 per view).  Timed
+    with the library's CUDA events, inputs resident; reports line-pair samples/s of the
+    whole call and the per-kernel times."""
+    import torch
+    import paper_1806_02637_gb300 as ecc
+    rng = np.random.default_rng(2024)
+    th = np.concatenate([rng.normal(0.0, np.deg2rad(1.0), (cfg.n_views, 3)),
+                         rng.normal(0.0, 2.0, (cfg.n_views, 3))], axis=1)
+    motion = torch.from_numpy(th).to(sino.device)
+    units = cfg.n_pairs * cfg.K
+    out = {}
+    for name, fn in (("motion_gradient", ecc.ecc_evaluate_grad),
+                     ("calibration_gradient", ecc.ecc_evaluate_grad_projection)):
+        for _ in range(2):
+            fn(ctx, P, sino, cfg.W, cfg.H, cfg.K, motion=motion, want_per_pair=False)
+        torch.cuda.synchronize()
+        ecc.ecc_profile_read(ctx)
+        ecc.ecc_profile_enable(ctx, True)
+        for _ in range(reps):
+            fn(ctx, P, sino, cfg.W, cfg.H, cfg.K, motion=motion, want_per_pair=False)
+        torch.cuda.synchronize()
+        prof = ecc.ecc_profile_read(ctx)
+        ecc.ecc_profile_enable(ctx, False)
+        ms = sum(t for _, t in prof.values()) / reps
+        out[name] = {"ms_per_call": ms, "line_pairs_per_s": units / (ms / 1e3),
+                     "kernels_ms": {k: t / reps for k, (c, t) in sorted(prof.items(), key=lambda kv: -kv[1][1])}}
+    out["note"] = ("ecc_evaluate_grad / ecc_evaluate_grad_projection on the FP32 sinograms of this scan, seeded "
+                   "motion, all pairs; the per-sample adjoint runs in the pair kernel (ecc_pair_grad_kernel)")
+    return out
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
@@ -512,6 +550,9 @@ def run_ours(args):
                      "pair_kernel_ms": pk["ms_per_step"],
                      "pair_kernel_gather_gbs": gbs,
                      "pair_kernel_frac_of_hbm": gbs / peaks.get("hbm_gbs", 6800.0)}
+    adjoint = None
+    if not args.no_adjoint_forms:
+        adjoint = adjoint_forms(ctx, P, sino, cfg)
     forms = None
     if not args.no_storage_forms:
         forms = storage_forms(ctx, P, images, cfg, result_total)
@@ -530,7 +571,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(cfg),
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
-            "kernels": kern, "ecc_eval_only": eval_only, "storage_forms": forms, "serving": serving,
+            "kernels": kern, "ecc_eval_only": eval_only, "storage_forms": forms, "adjoint_forms": adjoint,
+            "serving": serving,
             "total": result_total,
             "geometry_precision": "f64 per-view/per-pair set-up, double-float (~48-bit) tile anchors, f32 per-sample"}
     print(json.dumps(line), flush=True)

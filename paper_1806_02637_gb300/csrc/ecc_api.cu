@@ -42,8 +42,8 @@ struct ecc_ctx {
   std::string err;
   int* d_status = nullptr;
   Buf views, pairs, ctile, adir, perpair, nk, partial, rtable, wimg, stage;
-  Buf vtan, Gpp, gpp;  // adjoint scratch
-  Buf vtanP, gq;       // adjoint scratch of the gradient with respect to P
+  Buf vtan, Gpp, gq;  // adjoint scratch: view tangents (theta), d e / d A, d e / d (C, up, cofc)
+  Buf vtanP;          // view tangents with respect to P
   // sampling of the last evaluation (for ecc_evaluate_frozen)
   bool samp_valid = false;
   int samp_views = 0, samp_pairs = 0, samp_K = 0, samp_W = 0, samp_H = 0;
@@ -219,13 +219,14 @@ int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion,
   if (grad || grad_P) {
     if ((rc = ensure(c, c->Gpp, sizeof(double) * 12 * (size_t)np, "pair adjoints")) != ECC_OK) return rc;
   }
+  if (grad || grad_P) {
+    if ((rc = ensure(c, c->gq, sizeof(double) * 30 * (size_t)np, "pair q gradients")) != ECC_OK) return rc;
+  }
   if (grad) {
     if ((rc = ensure(c, c->vtan, sizeof(ecc::ViewTan) * (size_t)n_views, "view tangents")) != ECC_OK) return rc;
-    if ((rc = ensure(c, c->gpp, sizeof(double) * 12 * (size_t)np, "pair gradients")) != ECC_OK) return rc;
   }
   if (grad_P) {
     if ((rc = ensure(c, c->vtanP, sizeof(ecc::ViewTanP) * (size_t)n_views, "view P tangents")) != ECC_OK) return rc;
-    if ((rc = ensure(c, c->gq, sizeof(double) * 30 * (size_t)np, "pair q gradients")) != ECC_OK) return rc;
   }
   if (!reuse) c->samp_valid = false;
   const ecc::LaunchHooks hk = hooks_of(c);
@@ -252,22 +253,25 @@ int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion,
   if (e != cudaSuccess) return cuda_fail(c, e, "pair kernel launch");
   e = ecc::launch_reduce((const double*)c->partial.p, nb, total, hk, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "reduce launch");
+  if (grad || grad_P) {
+    // d e / d (C, up, cofc) per pair, shared by both gradients
+    hk.on_begin("pair_grad_q_kernel", s);
+    ecc::pair_grad_q_kernel<<<(unsigned)((np + 63) / 64), 64, 0, s>>>(np, (const ecc::PairRec*)c->pairs.p,
+                                                                      (const ecc::ViewRec*)c->views.p,
+                                                                      (const double*)c->Gpp.p, (double*)c->gq.p);
+    hk.on_end("pair_grad_q_kernel", s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "pair q gradient launch");
+  }
   if (grad) {
     hk.on_begin("view_tangent_kernel", s);
     ecc::view_tangent_kernel<<<(n_views + 63) / 64, 64, 0, s>>>(n_views, P, motion, W, H,
                                                                (ecc::ViewTan*)c->vtan.p);
     hk.on_end("view_tangent_kernel", s);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "view tangent launch");
-    hk.on_begin("pair_grad_kernel", s);
-    ecc::pair_grad_kernel<<<(unsigned)((np + 63) / 64), 64, 0, s>>>(np, (const ecc::PairRec*)c->pairs.p,
-                                                                    (const ecc::ViewRec*)c->views.p,
-                                                                    (const ecc::ViewTan*)c->vtan.p,
-                                                                    (const double*)c->Gpp.p, (double*)c->gpp.p);
-    hk.on_end("pair_grad_kernel", s);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "pair gradient launch");
-    hk.on_begin("view_grad_reduce_kernel", s);
-    ecc::view_grad_reduce_kernel<<<n_views, 256, 0, s>>>(n_views, np, pairs, (const double*)c->gpp.p, grad);
-    hk.on_end("view_grad_reduce_kernel", s);
+    hk.on_begin("view_grad_theta_kernel", s);
+    ecc::view_grad_theta_kernel<<<n_views, 256, 0, s>>>(n_views, np, pairs, (const double*)c->gq.p,
+                                                        (const ecc::ViewTan*)c->vtan.p, grad);
+    hk.on_end("view_grad_theta_kernel", s);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "gradient reduce launch");
   }
   if (grad_P) {
@@ -276,12 +280,6 @@ int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion,
                                                                        (ecc::ViewTanP*)c->vtanP.p);
     hk.on_end("view_tangent_P_kernel", s);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "view P tangent launch");
-    hk.on_begin("pair_grad_q_kernel", s);
-    ecc::pair_grad_q_kernel<<<(unsigned)((np + 63) / 64), 64, 0, s>>>(np, (const ecc::PairRec*)c->pairs.p,
-                                                                      (const ecc::ViewRec*)c->views.p,
-                                                                      (const double*)c->Gpp.p, (double*)c->gq.p);
-    hk.on_end("pair_grad_q_kernel", s);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "pair q gradient launch");
     hk.on_begin("view_grad_P_kernel", s);
     ecc::view_grad_P_kernel<<<n_views, 256, 0, s>>>(n_views, np, pairs, (const double*)c->gq.p,
                                                     (const ecc::ViewTanP*)c->vtanP.p, grad_P);
@@ -337,7 +335,7 @@ void ecc_destroy(ecc_ctx* c) {
   ecc::serve_destroy(c->serve);
   cudaDeviceSynchronize();
   Buf* bufs[] = {&c->views, &c->pairs, &c->ctile, &c->adir, &c->perpair, &c->nk, &c->partial, &c->rtable, &c->wimg,
-                 &c->vtan, &c->Gpp, &c->gpp, &c->vtanP, &c->gq, &c->stage, &c->h_P, &c->h_img, &c->h_sino, &c->h_total};
+                 &c->vtan, &c->Gpp, &c->gq, &c->vtanP, &c->stage, &c->h_P, &c->h_img, &c->h_sino, &c->h_total};
   for (Buf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->d_status) cudaFree(c->d_status);

@@ -2,15 +2,15 @@
 //
 // One warp owns one pair.  The pair's K sampled planes are processed in tiles of
 // 32 (one plane per lane).  For every tile and view the line of the tile centre is
-// an FP64 "anchor" (computed lane-parallel, one anchor per lane), split into an
-// exact (alpha row, s bin) integer part and an FP32 fraction; each lane then moves
-// from the anchor to its own plane with a cancellation-free FP32 formula for the
-// change of (alpha, s), so that the sinogram indices carry FP64-class accuracy
-// while the per-sample work stays in FP32.  Bilinear taps are gathered from the
-// L2-resident sinograms, squared differences are accumulated in FP32, reduced with
-// warp shuffles, normalised by N_kappa (Eq. 15), passed through the Cauchy norm
-// (Eq. 16) and summed per block in a fixed order (Eq. 17, finished by the reduce
-// kernel).
+// a double-float "anchor" (computed lane-parallel, one anchor per lane), split into
+// an exact (alpha row, s bin) integer part and an FP32 fraction, with the series of
+// the tile's offsets in t = tan(delta); each lane then moves from the anchor to its
+// own plane in FP32, so that the sinogram indices carry FP64-class accuracy while
+// the per-sample work stays in FP32.  Bilinear taps are gathered from the
+// sinograms, squared differences are accumulated in FP32, reduced with warp
+// shuffles, normalised by N_kappa (Eq. 15), passed through the Cauchy norm (Eq. 16)
+// and summed per block in a fixed order (Eq. 17, finished by the reduce kernel).
+// The adjoint variant also accumulates d e / d A for the gradient kernels.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -515,7 +515,8 @@ __device__ __forceinline__ float tile_diff(const float4* __restrict__ ra, const 
   return tile_diff_series<T, kSer>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f);
 }
 
-// Forward value of pair p on one warp: d, e and N_kappa (as pair_warp<T, false>).
+// Forward value of pair p on one warp (one plane per lane, tiles of 32): d (Eq. 15), the
+// Cauchy e (Eq. 16) and N_kappa.
 template <typename T>
 __device__ __forceinline__ double pair_warp_forward(const PairArgs& g, long long p, int lane,
                                                     float4* __restrict__ recw) {
@@ -609,158 +610,240 @@ __device__ __forceinline__ double pair_warp_forward(const PairArgs& g, long long
   return (double)e;
 }
 
-// One pair per warp (one plane per lane, tiles of 32): d, e and N_kappa of pair p
-// and, for GRAD, the adjoint d e / d A; returns e on every lane.  Inlined into the
-// single-scan kernel and the serving kernel; the two compiled copies may round
-// FP32 operations differently (1e-7 relative, well inside the FP32 bar), while
-// each kernel is deterministic.
-template <typename T, bool GRAD>
-__device__ __forceinline__ double pair_warp(const PairArgs& g, long long p, int lane, float4* __restrict__ recw) {
-  const PairRec* __restrict__ prs = g.prs;
-  const float4* __restrict__ ctile = g.ctile;
-  const int n_tiles = g.n_tiles;
-  const float4* __restrict__ alpha_dir = g.alpha_dir;
-  const T* __restrict__ sino = static_cast<const T*>(g.sino);
-  const float* __restrict__ scales = g.scales;
-  const int n_alpha = g.n_alpha, n_s = g.n_s, K = g.K;
-  const float cauchy_c = g.cauchy_c;
-  double* __restrict__ per_pair = g.per_pair;
-  int32_t* __restrict__ nk_out = g.nk_out;
-  double* __restrict__ Gpp = g.Gpp;
-  double e_val = 0.0;
+// ------------------------------------------------------------ adjoint fast path
+//
+// The adjoint kernel uses the forward kernel's positions (series_position) and warp
+// vote; the value and line gradient of a sample are those of sample_grad, written
+// for a row in [0, n_alpha - 2] and the anchor's fold.
+
+template <typename T>
+__device__ __forceinline__ float sample_grad_rows(const T* __restrict__ sv, int n_s, unsigned m, int n, float fa,
+                                                  float fs, float sign, float inv_dalpha, float inv_ds_f, float l0,
+                                                  float l1, float l2, float scale, float (&g)[3]) {
+  n = min(max(n, 0), n_s - 2);
+  const unsigned i0 = m * (unsigned)n_s + (unsigned)n;
+  const T* __restrict__ r0 = sv + i0;
+  const T* __restrict__ r1 = sv + (i0 + (unsigned)n_s);
+  const float t00 = Elem<T>::get(r0), t01 = Elem<T>::get(r0 + 1);
+  const float t10 = Elem<T>::get(r1), t11 = Elem<T>::get(r1 + 1);
+  const float dv0 = t01 - t00, dv1 = t11 - t10;
+  const float v0 = fmaf(fs, dv0, t00), v1 = fmaf(fs, dv1, t10);
+  const float Ba = (v1 - v0) * inv_dalpha * scale;
+  const float Bs = fmaf(fa, dv1 - dv0, dv0) * inv_ds_f * scale;
+  const float L0 = sign * l0, L1 = sign * l1, L2 = sign * l2;
+  const float ih = rsqrtf(fmaf(L0, L0, L1 * L1));
+  const float ca = L0 * ih, sa = L1 * ih, sf = -L2 * ih;
+  g[0] = ih * (-Ba * sa - Bs * sf * ca);
+  g[1] = ih * (Ba * ca - Bs * sf * sa);
+  g[2] = -ih * Bs;
+  return scale * sign * fmaf(fa, v1 - v0, v0);
+}
+
+// S_a - S_b of this lane's sample and the line gradients of both views, by the general
+// per-sample code.
+template <typename T>
+__device__ __forceinline__ float tile_adjoint_general_body(const float4* __restrict__ ra,
+                                                          const float4* __restrict__ rb, const LaneGeom& q,
+                                                          const T* __restrict__ sa, const T* __restrict__ sb,
+                                                          float sca, float scb, int n_alpha, int n_s,
+                                                          float inv_dalpha, float inv_ds_f, const float (&Af)[12],
+                                                          float ckx, float cky, float (&ga)[3], float (&gb)[3]) {
+  Loc la, lb;
   {
-    const PairRec& pr = prs[p];
-    const int status = pr.status;
-    const int nk = status == 0 ? pr.nk : 0;
-    float acc = 0.0f;
-    float G[12];  // adjoint only: sum_k 2 (S_a - S_b) (dS/dl) c_k^T for views a (0..5), b (6..11)
-#pragma unroll
-    for (int i = 0; i < 12; ++i) G[i] = 0.0f;
-    if (nk > 0) {
-      const size_t vstride = (size_t)n_alpha * n_s;
-      const T* sa = sino + (size_t)pr.a * vstride;
-      const T* sb = sino + (size_t)pr.b * vstride;
-      const float sca = scales ? scales[pr.a] : 1.0f;
-      const float scb = scales ? scales[pr.b] : 1.0f;
-      const float inv_dalpha = g.inv_dalpha;
-      const df inv_ds = {g.inv_ds_hi, g.inv_ds_lo};
-      const df half_ns1 = {g.half_hi, g.half_lo};
-      const float inv_ds_f = g.inv_ds_f;
-      // offset of this lane's plane from its tile centre: (j + 1/2 - n_t/2) dk for a
-      // tile of n_t samples (n_t = 32 except for the last tile)
-      const float dkf = pr.dk_hi;
-      const df dk = {pr.dk_hi, pr.dk_lo};
-      const float jj_full = (float)lane - 15.5f;
-      const float jj_last = (float)lane + 0.5f - 0.5f * (float)(K - 32 * (n_tiles - 1));
-      const float de_full = jj_full * dkf, de_last = jj_last * dkf;
-      float sd, cd, sd_last, cd_last;
-      sincosf(de_full, &sd, &cd);
-      sincosf(de_last, &sd_last, &cd_last);
-      const float t_full = tanf(de_full), t_last = tanf(de_last);
-      const float tmd_full = tan_minus_angle(de_full, t_full), tmd_last = tan_minus_angle(de_last, t_last);
-      const float tan_half_tile = tanf(15.5f * dkf);
-      const int r0lo = pr.r0lo, r0hi = pr.r0hi, r1lo = pr.r1lo, r1hi = pr.r1hi;
-      const float4* ct = ctile + p * n_tiles;
-      float Af[12];
-      if (GRAD) {
-#pragma unroll
-        for (int i = 0; i < 12; ++i) Af[i] = (&pr.Af[0][0])[2 * i];
-      }
-      for (int t0 = 0; t0 < n_tiles; t0 += 16) {
-        {
-          const int v = lane >> 4;
-          int t = t0 + (lane & 15);
-          if (t >= n_tiles) t = n_tiles - 1;
-          store_anchor(recw + 8 * lane, make_anchor(pr.Af[v], ct[t], alpha_dir, n_alpha, inv_dalpha, inv_ds,
-                                                    half_ns1, inv_ds_f, dk, tan_half_tile));
-        }
-        __syncwarp();
-        const int tmax = min(16, n_tiles - t0);
-        for (int tt = 0; tt < tmax; ++tt) {
-          const int k = 32 * (t0 + tt) + lane;
-          const bool valid = k < K && ((k >= r0lo && k < r0hi) || (k >= r1lo && k < r1hi));
-          const bool last = t0 + tt == n_tiles - 1;
-          const float c_ = last ? cd_last : cd, s_ = last ? sd_last : sd;
-          const float jj = last ? jj_last : jj_full, de = last ? de_last : de_full;
-          const float t_ = last ? t_last : t_full, tmd_ = last ? tmd_last : tmd_full;
-          Loc la, lb;
-          {
-            const Anchor an = load_anchor(recw + 8 * tt);
-            la = an.ser != 0.0f ? locate_series(an, t_, tmd_, jj, n_alpha, n_s)  // warp-uniform choice
-                                : locate(an, c_, s_, jj, de, n_alpha, n_s, inv_dalpha, inv_ds_f);
-          }
-          {
-            const Anchor an = load_anchor(recw + 8 * (16 + tt));
-            lb = an.ser != 0.0f ? locate_series(an, t_, tmd_, jj, n_alpha, n_s)
-                                : locate(an, c_, s_, jj, de, n_alpha, n_s, inv_dalpha, inv_ds_f);
-          }
-          if (!GRAD) {
-            const float Sa = sca * sample(sa, n_alpha, n_s, la);
-            const float Sb = scb * sample(sb, n_alpha, n_s, lb);
-            const float dd = Sa - Sb;
-            acc += valid ? dd * dd : 0.0f;
-          } else {
-            // this lane's plane direction c_k in the (w, v) frame
-            const float4 ctd = ct[t0 + tt];
-            const float cx = ctd.x, cy = ctd.y;
-            const float ckx = cx * c_ - cy * s_, cky = cx * s_ + cy * c_;
-            float ga[3], gb[3];
-            const float Sa = sample_grad(sa, n_alpha, n_s, la, inv_dalpha, inv_ds_f, Af[0] * ckx + Af[1] * cky,
-                                         Af[2] * ckx + Af[3] * cky, Af[4] * ckx + Af[5] * cky, sca, ga);
-            const float Sb = sample_grad(sb, n_alpha, n_s, lb, inv_dalpha, inv_ds_f, Af[6] * ckx + Af[7] * cky,
-                                         Af[8] * ckx + Af[9] * cky, Af[10] * ckx + Af[11] * cky, scb, gb);
-            const float dd = Sa - Sb;
-            acc += valid ? dd * dd : 0.0f;
-            const float w2 = valid ? 2.0f * dd : 0.0f;
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-              G[2 * i] = fmaf(w2 * ga[i], ckx, G[2 * i]);
-              G[2 * i + 1] = fmaf(w2 * ga[i], cky, G[2 * i + 1]);
-              G[6 + 2 * i] = fmaf(-w2 * gb[i], ckx, G[6 + 2 * i]);
-              G[6 + 2 * i + 1] = fmaf(-w2 * gb[i], cky, G[6 + 2 * i + 1]);
-            }
-          }
-        }
-        __syncwarp();  // records are rewritten by the next chunk
-      }
-    }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (GRAD) {
-#pragma unroll
-      for (int i = 0; i < 12; ++i)
-        for (int o = 16; o > 0; o >>= 1) G[i] += __shfl_xor_sync(0xffffffffu, G[i], o);
-    }
-    const float d = nk > 0 ? acc / (float)nk : 0.0f;
-    const float e = cauchy_c > 0.0f ? d / (1.0f + d / cauchy_c) : d;
-    if (lane == 0) {
-      if (per_pair) {
-        per_pair[2 * p] = (double)d;
-        per_pair[2 * p + 1] = (double)e;
-      }
-      if (nk_out) nk_out[p] = nk;
-      if (GRAD) {
-        // d e / d A = (de/dd) (1/N) G
-        const float r = cauchy_c > 0.0f ? 1.0f / (1.0f + d / cauchy_c) : 1.0f;
-        const float scale = nk > 0 ? r * r / (float)nk : 0.0f;
-#pragma unroll
-        for (int i = 0; i < 12; ++i) Gpp[12 * p + i] = (double)(G[i] * scale);
-      }
-    }
-    e_val = (double)e;
+    const Anchor an = load_anchor(ra);
+    la = an.ser != 0.0f ? locate_series(an, q.t, q.tmd, q.jj, n_alpha, n_s)
+                        : locate(an, q.cd, q.sd, q.jj, q.de, n_alpha, n_s, inv_dalpha, inv_ds_f);
   }
-  return e_val;
+  {
+    const Anchor an = load_anchor(rb);
+    lb = an.ser != 0.0f ? locate_series(an, q.t, q.tmd, q.jj, n_alpha, n_s)
+                        : locate(an, q.cd, q.sd, q.jj, q.de, n_alpha, n_s, inv_dalpha, inv_ds_f);
+  }
+  const float Sa = sample_grad(sa, n_alpha, n_s, la, inv_dalpha, inv_ds_f, Af[0] * ckx + Af[1] * cky,
+                               Af[2] * ckx + Af[3] * cky, Af[4] * ckx + Af[5] * cky, sca, ga);
+  const float Sb = sample_grad(sb, n_alpha, n_s, lb, inv_dalpha, inv_ds_f, Af[6] * ckx + Af[7] * cky,
+                               Af[8] * ckx + Af[9] * cky, Af[10] * ckx + Af[11] * cky, scb, gb);
+  return Sa - Sb;
+}
+
+template <typename T>
+__device__ __noinline__ float tile_adjoint_general(const float4* __restrict__ ra, const float4* __restrict__ rb,
+                                                  const LaneGeom& q, const T* __restrict__ sa,
+                                                  const T* __restrict__ sb, float sca, float scb, int n_alpha,
+                                                  int n_s, float inv_dalpha, float inv_ds_f,
+                                                  const float (&Af)[12], float ckx, float cky, float (&ga)[3],
+                                                  float (&gb)[3]) {
+  return tile_adjoint_general_body<T>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f, Af, ckx, cky,
+                                      ga, gb);
+}
+
+template <typename T, int NT>
+__device__ __forceinline__ float tile_adjoint_series(const float4* __restrict__ ra, const float4* __restrict__ rb,
+                                                    const LaneGeom& q, const T* __restrict__ sa,
+                                                    const T* __restrict__ sb, float sca, float scb, int n_alpha,
+                                                    int n_s, float inv_dalpha, float inv_ds_f,
+                                                    const float (&Af)[12], float ckx, float cky, float (&ga)[3],
+                                                    float (&gb)[3]) {
+  unsigned ma, mb;
+  int na, nb;
+  float faa, fsa, fab, fsb;
+  series_position<NT>(ra, q, ma, na, faa, fsa);
+  series_position<NT>(rb, q, mb, nb, fab, fsb);
+  const unsigned last = (unsigned)(n_alpha - 1);
+  if (__any_sync(0xffffffffu, ma >= last || mb >= last))
+    return tile_adjoint_general<T>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f, Af, ckx, cky,
+                                   ga, gb);
+  const float Sa = sample_grad_rows(sa, n_s, ma, na, faa, fsa, ra[1].x, inv_dalpha, inv_ds_f,
+                                    Af[0] * ckx + Af[1] * cky, Af[2] * ckx + Af[3] * cky, Af[4] * ckx + Af[5] * cky,
+                                    sca, ga);
+  const float Sb = sample_grad_rows(sb, n_s, mb, nb, fab, fsb, rb[1].x, inv_dalpha, inv_ds_f,
+                                    Af[6] * ckx + Af[7] * cky, Af[8] * ckx + Af[9] * cky,
+                                    Af[10] * ckx + Af[11] * cky, scb, gb);
+  return Sa - Sb;
+}
+
+template <typename T>
+__device__ __forceinline__ float tile_adjoint(const float4* __restrict__ ra, const float4* __restrict__ rb,
+                                             const LaneGeom& q, const T* __restrict__ sa, const T* __restrict__ sb,
+                                             float sca, float scb, int n_alpha, int n_s, float inv_dalpha,
+                                             float inv_ds_f, const float (&Af)[12], float ckx, float cky,
+                                             float (&ga)[3], float (&gb)[3]) {
+  const float na = ra[1].w, nb = rb[1].w;
+  if (na == 0.0f || nb == 0.0f)
+    return tile_adjoint_general<T>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f, Af, ckx, cky,
+                                   ga, gb);
+  const float nt = fmaxf(na, nb);
+#define ECC_ADJ(NT_) \
+  return tile_adjoint_series<T, NT_>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f, Af, ckx, cky, ga, gb)
+  if (nt <= 3.0f) ECC_ADJ(3);
+  if (nt <= 4.0f) ECC_ADJ(4);
+  if (nt <= 6.0f) ECC_ADJ(6);
+  if (nt <= 8.0f) ECC_ADJ(8);
+  ECC_ADJ(kSer);
+#undef ECC_ADJ
+}
+
+// Adjoint of pair p on one warp: d, e, N_kappa as the forward kernel, and d e / d A
+// (de/dd)/N_kappa sum_k 2 (S_a - S_b) (dS/dl) c_k^T for the gradient kernels.
+// FAST: tiles dispatch on the anchors' term counts (the single-scan kernel); otherwise
+// every tile takes the general per-sample code inline (the persistent serving kernel,
+// whose three storage types would otherwise carry fifteen tile variants; same positions
+// and formulas, so the same values).
+template <typename T, bool FAST>
+__device__ __forceinline__ double pair_warp_adjoint(const PairArgs& g, long long p, int lane,
+                                                    float4* __restrict__ recw) {
+  const PairRec& pr = g.prs[p];
+  const int nk = pr.status == 0 ? pr.nk : 0;
+  const int n_tiles = g.n_tiles, n_alpha = g.n_alpha, n_s = g.n_s, K = g.K;
+  float acc = 0.0f;
+  float G[12];  // sum_k 2 (S_a - S_b) (dS/dl) c_k^T for views a (0..5), b (6..11)
+#pragma unroll
+  for (int i = 0; i < 12; ++i) G[i] = 0.0f;
+  if (nk > 0) {
+    const T* __restrict__ sino = static_cast<const T*>(g.sino);
+    const size_t vstride = (size_t)n_alpha * n_s;
+    const T* __restrict__ sa = sino + (size_t)pr.a * vstride;
+    const T* __restrict__ sb = sino + (size_t)pr.b * vstride;
+    const float sca = g.scales ? g.scales[pr.a] : 1.0f;
+    const float scb = g.scales ? g.scales[pr.b] : 1.0f;
+    const float inv_dalpha = g.inv_dalpha, inv_ds_f = g.inv_ds_f;
+    const df inv_ds = {g.inv_ds_hi, g.inv_ds_lo};
+    const df half_ns1 = {g.half_hi, g.half_lo};
+    const float dkf = pr.dk_hi;
+    const df dk = {pr.dk_hi, pr.dk_lo};
+    auto lane_geom = [&](float jj) {
+      LaneGeom q;
+      q.jj = jj;
+      q.de = jj * dkf;
+      sincosf(q.de, &q.sd, &q.cd);
+      q.t = tanf(q.de);
+      q.t2 = q.t * q.t;
+      q.tmd = tan_minus_angle(q.de, q.t);
+      return q;
+    };
+    const int n_last = K - 32 * (n_tiles - 1);
+    const LaneGeom qf = lane_geom((float)lane - 15.5f);
+    const LaneGeom ql = lane_geom((float)lane + 0.5f - 0.5f * (float)n_last);
+    const float tan_half_tile = tanf(15.5f * dkf);
+    const int r0lo = pr.r0lo, r1lo = pr.r1lo;
+    const unsigned len0 = (unsigned)max(pr.r0hi - pr.r0lo, 0), len1 = (unsigned)max(pr.r1hi - pr.r1lo, 0);
+    const float4* __restrict__ ct = g.ctile + p * n_tiles;
+    float Af[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) Af[i] = (&pr.Af[0][0])[2 * i];
+    auto one_tile = [&](int t, const LaneGeom& q, bool valid) {
+      const float4 ctd = ct[t];
+      const float ckx = ctd.x * q.cd - ctd.y * q.sd, cky = ctd.x * q.sd + ctd.y * q.cd;
+      float ga[3], gb[3];
+      const int tt = t & 15;
+      const float dd =
+          FAST ? tile_adjoint<T>(recw + 8 * tt, recw + 8 * (16 + tt), q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha,
+                                 inv_ds_f, Af, ckx, cky, ga, gb)
+               : tile_adjoint_general_body<T>(recw + 8 * tt, recw + 8 * (16 + tt), q, sa, sb, sca, scb, n_alpha,
+                                              n_s, inv_dalpha, inv_ds_f, Af, ckx, cky, ga, gb);
+      acc += valid ? dd * dd : 0.0f;
+      const float w2 = valid ? 2.0f * dd : 0.0f;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        G[2 * i] = fmaf(w2 * ga[i], ckx, G[2 * i]);
+        G[2 * i + 1] = fmaf(w2 * ga[i], cky, G[2 * i + 1]);
+        G[6 + 2 * i] = fmaf(-w2 * gb[i], ckx, G[6 + 2 * i]);
+        G[6 + 2 * i + 1] = fmaf(-w2 * gb[i], cky, G[6 + 2 * i + 1]);
+      }
+    };
+    for (int t0 = 0; t0 < n_tiles; t0 += 16) {
+      {
+        const int v = lane >> 4;
+        int t = t0 + (lane & 15);
+        if (t >= n_tiles) t = n_tiles - 1;
+        store_anchor(recw + 8 * lane, make_anchor(pr.Af[v], ct[t], g.alpha_dir, n_alpha, inv_dalpha, inv_ds,
+                                                  half_ns1, inv_ds_f, dk, tan_half_tile));
+      }
+      __syncwarp();
+      const int tmax = min(16, n_tiles - t0);
+      const int tfull = (t0 + tmax == n_tiles && n_last != 32) ? tmax - 1 : tmax;
+      for (int tt = 0; tt < tfull; ++tt) {
+        const int k = 32 * (t0 + tt) + lane;
+        one_tile(t0 + tt, qf, (unsigned)(k - r0lo) < len0 || (unsigned)(k - r1lo) < len1);
+      }
+      if (tfull < tmax) {
+        const int k = 32 * (t0 + tfull) + lane;
+        one_tile(t0 + tfull, ql, k < K && ((unsigned)(k - r0lo) < len0 || (unsigned)(k - r1lo) < len1));
+      }
+      __syncwarp();
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+#pragma unroll
+  for (int i = 0; i < 12; ++i)
+    for (int o = 16; o > 0; o >>= 1) G[i] += __shfl_xor_sync(0xffffffffu, G[i], o);
+  const float d = nk > 0 ? acc / (float)nk : 0.0f;
+  const float e = g.cauchy_c > 0.0f ? d / (1.0f + d / g.cauchy_c) : d;
+  if (lane == 0) {
+    if (g.per_pair) {
+      g.per_pair[2 * p] = (double)d;
+      g.per_pair[2 * p + 1] = (double)e;
+    }
+    if (g.nk_out) g.nk_out[p] = nk;
+    // d e / d A = (de/dd) (1/N) G
+    const float r = g.cauchy_c > 0.0f ? 1.0f / (1.0f + d / g.cauchy_c) : 1.0f;
+    const float scale = nk > 0 ? r * r / (float)nk : 0.0f;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) g.Gpp[12 * p + i] = (double)(G[i] * scale);
+  }
+  return (double)e;
 }
 
 // One block of kWarpsPerBlock consecutive pairs: their e summed in a fixed order
 // into partial[blk].
-template <typename T, bool GRAD>
+template <typename T, bool GRAD, bool SERVE = false>
 __device__ __forceinline__ void pair_block(const PairArgs& g, long long blk, double* e_warp, float4* recs) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long p = blk * kWarpsPerBlock + wib;
   double e_val = 0.0;
   if (p < g.n_pairs) {  // warp-uniform
     float4* recw = recs + (size_t)wib * 32 * 8;
-    e_val = GRAD ? pair_warp<T, true>(g, p, lane, recw) : pair_warp_forward<T>(g, p, lane, recw);
+    e_val = GRAD ? pair_warp_adjoint<T, !SERVE>(g, p, lane, recw) : pair_warp_forward<T>(g, p, lane, recw);
   }
   if (lane == 0) e_warp[wib] = e_val;
   __syncthreads();
@@ -824,15 +907,15 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 3) serve_pair_kernel(cons
     const int j = serve_job_of(boff, n_jobs, it);
     const PairArgs g = jobs[j].pair;
     const long long blk = it - boff[j];
-    switch (jobs[j].dtype) {
+    switch (jobs[j].dtype) {  // block-uniform
       case 0:
-        pair_block<float, true>(g, blk, e_warp, recs);
+        pair_block<float, true, true>(g, blk, e_warp, recs);
         break;
       case 1:
-        pair_block<__half, true>(g, blk, e_warp, recs);
+        pair_block<__half, true, true>(g, blk, e_warp, recs);
         break;
       default:
-        pair_block<__nv_bfloat16, true>(g, blk, e_warp, recs);
+        pair_block<__nv_bfloat16, true, true>(g, blk, e_warp, recs);
         break;
     }
   }

@@ -425,57 +425,6 @@ __global__ void pair_setup_kernel(int n_views, long long n_pairs, const int32_t*
   out[p] = r;
 }
 
-// Gradient of one pair's e with respect to the 12 motion parameters of its two
-// views: the frame (w, v) and the kappa -> line maps A = cof(M) [w v] are
-// recomputed with forward-mode tangents (FP64), then contracted with
-// G = d e / d A accumulated by the pair kernel (already scaled by de/dd / N).
-__device__ void pair_grad(const PairRec& pr, const ViewRec* __restrict__ views, const ViewTan* __restrict__ vtan,
-                          const double* __restrict__ G, double* __restrict__ out) {
-  if (pr.status != 0 || pr.nk <= 0) {
-    for (int j = 0; j < 12; ++j) out[j] = 0.0;
-    return;
-  }
-  using D = Dual<12>;
-  const int ab[2] = {pr.a, pr.b};
-  D C[2][3], up[2][3], cof[2][9];
-  for (int s = 0; s < 2; ++s) {
-    const ViewRec& vr = views[ab[s]];
-    const ViewTan& vt = vtan[ab[s]];
-    for (int k = 0; k < 3; ++k) {
-      C[s][k] = D(vr.C[k]);
-      up[s][k] = D(vr.up[k]);
-      for (int j = 0; j < 6; ++j) {
-        C[s][k].d[6 * s + j] = vt.dC[k][j];
-        up[s][k].d[6 * s + j] = vt.dup[k][j];
-      }
-    }
-    for (int k = 0; k < 9; ++k) {
-      cof[s][k] = D(vr.cofc[k]);
-      for (int j = 0; j < 6; ++j) cof[s][k].d[6 * s + j] = vt.dcofc[k][j];
-    }
-  }
-  D w[3], v[3];
-  pencil_frame(C[0], C[1], up[0], up[1], w, v);
-  double g[12];
-  for (int j = 0; j < 12; ++j) g[j] = 0.0;
-  for (int s = 0; s < 2; ++s)
-    for (int i = 0; i < 3; ++i) {
-      const D aw = dot3(cof[s] + 3 * i, w);
-      const D av = dot3(cof[s] + 3 * i, v);
-      const double g0 = G[6 * s + 2 * i], g1 = G[6 * s + 2 * i + 1];
-      for (int j = 0; j < 12; ++j) g[j] += g0 * aw.d[j] + g1 * av.d[j];
-    }
-  for (int j = 0; j < 12; ++j) out[j] = g[j];
-}
-
-__global__ void pair_grad_kernel(long long n_pairs, const PairRec* __restrict__ prs,
-                                 const ViewRec* __restrict__ views, const ViewTan* __restrict__ vtan,
-                                 const double* __restrict__ Gpp, double* __restrict__ gpp) {
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n_pairs) return;
-  pair_grad(prs[p], views, vtan, Gpp + 12 * p, gpp + 12 * p);
-}
-
 // Gradient of one pair's e with respect to the per-view quantities the pair reads,
 // q = (C[3], up[3], cofc[9]) of view a, then of view b (30 values): the frame
 // (w, v) carries forward-mode tangents in the sources and up axes (12
@@ -524,15 +473,12 @@ __global__ void pair_grad_q_kernel(long long n_pairs, const PairRec* __restrict_
   pair_grad_q(prs[p], views, Gpp + 12 * p, gq + 30 * p);
 }
 
-// Per-view sum of the pairs' q gradients in a fixed order (one block per view),
-// contracted with the view's tangents: grad_P[view][12] = sum_k dtotal/dq_k dq_k/dP.
-__global__ void __launch_bounds__(256) view_grad_P_kernel(int n_views, long long n_pairs,
-                                                          const int32_t* __restrict__ pairs,
-                                                          const double* __restrict__ gq,
-                                                          const ViewTanP* __restrict__ vtan,
-                                                          double* __restrict__ grad_P) {
-  __shared__ double sh[15][256];
-  const int lam = blockIdx.x;
+// Per-view sum of the pairs' q gradients in a fixed order (one block of 256 threads
+// per view): on return sh[k][0] (k < 15) holds d total / d q_k of view lam.  With
+// pairs == NULL the pairs of a view are found by the row-major a < b enumeration,
+// otherwise by scanning the pair list.
+__device__ void reduce_q_block(int lam, int n_views, long long n_pairs, const int32_t* __restrict__ pairs,
+                               const double* __restrict__ gq, double (*sh)[256]) {
   double acc[15];
   for (int k = 0; k < 15; ++k) acc[k] = 0.0;
   if (pairs) {
@@ -560,55 +506,45 @@ __global__ void __launch_bounds__(256) view_grad_P_kernel(int n_views, long long
       for (int k = 0; k < 15; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + wdt];
     __syncthreads();
   }
+}
+
+// d total / d theta of one view from its q gradient (sh[k][0]) and the tangents
+// d q / d theta (C, up, cofc rows).
+__device__ __forceinline__ double contract_theta(const double (*sh)[256], const ViewTan& t, int j) {
+  double g = 0.0;
+  for (int k = 0; k < 3; ++k) g += sh[k][0] * t.dC[k][j];
+  for (int k = 0; k < 3; ++k) g += sh[3 + k][0] * t.dup[k][j];
+  for (int k = 0; k < 9; ++k) g += sh[6 + k][0] * t.dcofc[k][j];
+  return g;
+}
+
+// grad[view][6] = d total / d theta (one block of 256 threads per view).
+__global__ void __launch_bounds__(256) view_grad_theta_kernel(int n_views, long long n_pairs,
+                                                              const int32_t* __restrict__ pairs,
+                                                              const double* __restrict__ gq,
+                                                              const ViewTan* __restrict__ vtan,
+                                                              double* __restrict__ grad) {
+  __shared__ double sh[15][256];
+  const int lam = blockIdx.x;
+  reduce_q_block(lam, n_views, n_pairs, pairs, gq, sh);
+  if (threadIdx.x < 6) grad[6 * lam + threadIdx.x] = contract_theta(sh, vtan[lam], threadIdx.x);
+}
+
+// grad_P[view][12] = d total / d P (one block of 256 threads per view).
+__global__ void __launch_bounds__(256) view_grad_P_kernel(int n_views, long long n_pairs,
+                                                          const int32_t* __restrict__ pairs,
+                                                          const double* __restrict__ gq,
+                                                          const ViewTanP* __restrict__ vtan,
+                                                          double* __restrict__ grad_P) {
+  __shared__ double sh[15][256];
+  const int lam = blockIdx.x;
+  reduce_q_block(lam, n_views, n_pairs, pairs, gq, sh);
   if (threadIdx.x < 12) {
     const ViewTanP& t = vtan[lam];
     double g = 0.0;
     for (int k = 0; k < 15; ++k) g += sh[k][0] * t.d[k][threadIdx.x];
     grad_P[12 * lam + threadIdx.x] = g;
   }
-}
-
-// Per-view sum of the pair gradients in a fixed order (one block per view):
-// deterministic grad[view][6].  With pairs == NULL the pairs of a view are found
-// by the row-major a < b enumeration, otherwise by scanning the pair list.
-__device__ void view_grad_block(int lam, int n_views, long long n_pairs, const int32_t* __restrict__ pairs,
-                                const double* __restrict__ gpp, double* __restrict__ grad, double (*sh)[256]) {
-  double acc[6] = {0, 0, 0, 0, 0, 0};
-  if (pairs) {
-    for (long long p = threadIdx.x; p < n_pairs; p += blockDim.x) {
-      const int a = pairs[2 * p], b = pairs[2 * p + 1];
-      if (a == lam)
-        for (int j = 0; j < 6; ++j) acc[j] += gpp[12 * p + j];
-      if (b == lam)
-        for (int j = 0; j < 6; ++j) acc[j] += gpp[12 * p + 6 + j];
-    }
-  } else {
-    const long long n = n_views;
-    for (int o = threadIdx.x; o < n_views; o += blockDim.x) {
-      if (o == lam) continue;
-      const long long a = o < lam ? o : lam, b = o < lam ? lam : o;
-      const long long p = a * (2 * n - a - 1) / 2 + (b - a - 1);
-      const int off = o < lam ? 6 : 0;  // this view is b of the pair when o < lam
-      for (int j = 0; j < 6; ++j) acc[j] += gpp[12 * p + off + j];
-    }
-  }
-  for (int j = 0; j < 6; ++j) sh[j][threadIdx.x] = acc[j];
-  __syncthreads();
-  for (int wdt = blockDim.x / 2; wdt > 0; wdt >>= 1) {
-    if (threadIdx.x < wdt)
-      for (int j = 0; j < 6; ++j) sh[j][threadIdx.x] += sh[j][threadIdx.x + wdt];
-    __syncthreads();
-  }
-  if (threadIdx.x < 6) grad[6 * lam + threadIdx.x] = sh[threadIdx.x][0];
-  __syncthreads();
-}
-
-__global__ void __launch_bounds__(256) view_grad_reduce_kernel(int n_views, long long n_pairs,
-                                                               const int32_t* __restrict__ pairs,
-                                                               const double* __restrict__ gpp,
-                                                               double* __restrict__ grad) {
-  __shared__ double sh[6][256];
-  view_grad_block(blockIdx.x, n_views, n_pairs, pairs, gpp, grad, sh);
 }
 
 // ---------------------------------------------------------------- serving rounds
@@ -648,17 +584,19 @@ __global__ void serve_pair_grad_kernel(const ServeJob* __restrict__ jobs, const 
   const ServeJob& J = jobs[j];
   if (!J.do_grad) return;
   const long long p = i - poff[j];
-  pair_grad(J.pair.prs[p], J.views, J.vtan, J.pair.Gpp + 12 * p, J.gpp + 12 * p);
+  pair_grad_q(J.pair.prs[p], J.views, J.pair.Gpp + 12 * p, J.gpp + 30 * p);
 }
 
 __global__ void __launch_bounds__(256) serve_view_grad_kernel(const ServeJob* __restrict__ jobs,
                                                               const long long* __restrict__ voff, int n_jobs) {
-  __shared__ double sh[6][256];
+  __shared__ double sh[15][256];
   const long long i = blockIdx.x;
   const int j = serve_job_of(voff, n_jobs, i);
   const ServeJob& J = jobs[j];
   if (!J.do_grad) return;  // block-uniform
-  view_grad_block((int)(i - voff[j]), J.n_views, J.pair.n_pairs, nullptr, J.gpp, J.grad, sh);
+  const int lam = (int)(i - voff[j]);
+  reduce_q_block(lam, J.n_views, J.pair.n_pairs, nullptr, J.gpp, sh);
+  if (threadIdx.x < 6) J.grad[6 * lam + threadIdx.x] = contract_theta(sh, J.vtan[lam], threadIdx.x);
 }
 
 // Per-view jobs: theta <- theta - step * grad for the estimated parameters.

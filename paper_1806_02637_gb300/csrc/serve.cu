@@ -81,7 +81,7 @@ Layout layout_of(const ecc_job& j) {
   L.ctile = take(np * n_tiles * sizeof(float4));
   L.partial = take((np + kWarpsPerPairBlock - 1) / kWarpsPerPairBlock * sizeof(double));
   L.Gpp = take(np * 12 * sizeof(double));
-  L.gpp = take(np * 12 * sizeof(double));
+  L.gpp = take(np * 30 * sizeof(double));
   L.totals = take(((size_t)j.n_iters + 1) * sizeof(double));
   L.status = take(sizeof(int));
   L.theta0 = take(n * 6 * sizeof(double));
