@@ -137,13 +137,15 @@ def test_ecc_parity_motion_cauchy_pair_list():
     _check_pairs(sc["P"], S32, cfg.W, cfg.H, cfg.K, c=c, motion=sc["motion"], pairs=pairs)
 
 
-def test_ecc_full_scan_with_opposed_views():
-    """Full 360-degree geometry: opposed views take the full-pi arc branch."""
+@pytest.mark.parametrize("K", [256, 77])
+def test_ecc_full_scan_with_opposed_views(K):
+    """Full 360-degree geometry: opposed views take the full-pi arc branch (tiles cross
+    the alpha fold); K = 77 adds a ragged last tile."""
     cfg = synth.CONFIGS["c4"]
     views = (0, 1, 310, 619, 620, 621, 930, 1239)
     sc = H.scan("c4", views)
     S32 = orc.radon_derivative(sc["P"], sc["images"], 256, 346).astype(np.float32)
-    _, _, nk, ref = _check_pairs(sc["P"], S32, cfg.W, cfg.H, 256)
+    _, _, nk, ref = _check_pairs(sc["P"], S32, cfg.W, cfg.H, K)
     full = ref["arcs"][:, 2] > 3.14
     assert full.any()
 
