@@ -157,7 +157,7 @@ def test_autograd_function():
     r = ecc.ecc_evaluate_grad(_ctx(), P, S32, cfg.W, cfg.H, cfg.K, motion=m.detach())
     torch.cuda.synchronize()
     assert torch.allclose(gm, 2.0 * r["grad"], rtol=0, atol=0)
-    assert float(tot) == float(r["total"][0])
+    assert float(tot.detach()) == float(r["total"][0])
 
 
 def test_c3_full_size_gradient():
