@@ -8,6 +8,7 @@
 //                     Eq. 13/14), valid arcs from the detector corners, the sampled
 //                     arc, the integer ranges of valid samples and the direction of
 //                     each 32-sample tile centre.
+#include "df.cuh"
 #include "dual.cuh"
 #include "motion.cuh"
 #include "ecc_internal.cuh"
@@ -374,19 +375,22 @@ __host__ __device__ PairRec setup_pair(int a, int b, int n_views, const ViewRec*
     for (int i = 0; i < 4; ++i) twice(s16, c16);  // 16 dk
     double s32 = s16, c32 = c16;
     twice(s32, c32);  // 32 dk
-    double cx0 = c16 * csx - s16 * csy;
-    double cy0 = s16 * csx + c16 * csy;
+    // full tiles step by 32 dk: the rotation runs in double-float on the FP32 pipes
+    // (about 1e-13 rad per step; FP64 is issued at 1/64 of the FP32 rate)
+    df cx0 = df_from_double(c16 * csx - s16 * csy);
+    df cy0 = df_from_double(s16 * csx + c16 * csy);
+    const df c32d = df_from_double(c32), s32d = df_from_double(s32);
     float4* ct = ctile;
     for (int t = 0; t < n_tiles; ++t) {
       if (32 * t + 32 <= K) {
-        ct[t] = split_dir(cx0, cy0);
+        ct[t] = make_float4(cx0.hi, cy0.hi, cx0.lo, cy0.lo);
       } else {  // last, partial tile
         double sp, cp;
         sincos(0.5 * (32.0 * t + K) * dk, &sp, &cp);
         ct[t] = split_dir(cp * csx - sp * csy, sp * csx + cp * csy);
       }
-      const double nx = c32 * cx0 - s32 * cy0;
-      const double ny = s32 * cx0 + c32 * cy0;
+      const df nx = df_sub(df_mul(c32d, cx0), df_mul(s32d, cy0));
+      const df ny = df_add(df_mul(s32d, cx0), df_mul(c32d, cy0));
       cx0 = nx;
       cy0 = ny;
     }
