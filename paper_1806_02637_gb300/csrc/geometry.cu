@@ -136,6 +136,71 @@ __host__ __device__ bool pencil_frame(const T* Ca, const T* Cb, const T* upa, co
   return true;
 }
 
+// Reverse mode of pencil_frame (FP64): given gw = d e / d w and gv = d e / d v, adds
+// d e / d (Ca, Cb, upa, upb) to gCa, gCb and gup (the same for both up axes, which
+// enter as their sum); also returns w and v.  Each step's adjoint follows from its
+// forward rule: v = w x u gives w' += u x v', u' += v' x w; y = x / |x| gives
+// x' = (y' - (y'.y) y) / |x|; w_t = r - (r.u) u gives r' = w_t' - (w_t'.u) u and
+// u' -= (w_t'.u) r + (r.u) w_t' (for the fallback axis e: u' -= (w_t'.u) e_ax + u_ax w_t').
+__host__ __device__ bool pencil_frame_adjoint(const double* Ca, const double* Cb, const double* upa,
+                                              const double* upb, const double* gw, const double* gv,
+                                              double* w, double* v, double* gCa, double* gCb, double* gup) {
+  double d[3] = {Cb[0] - Ca[0], Cb[1] - Ca[1], Cb[2] - Ca[2]};
+  const double nd = sqrt(dot3(d, d));
+  if (!(nd > 0.0)) return false;
+  double u[3];
+  for (int k = 0; k < 3; ++k) u[k] = d[k] / nd;
+  double rr[3] = {upa[0] + upb[0], upa[1] + upb[1], upa[2] + upb[2]};
+  const double ru = dot3(rr, u);
+  double wt[3];
+  for (int k = 0; k < 3; ++k) wt[k] = rr[k] - ru * u[k];
+  double nw = sqrt(dot3(wt, wt));
+  int ax = -1;
+  if (nw < 1e-6) {
+    ax = 0;
+    double best = fabs(u[0]);
+    for (int k = 1; k < 3; ++k)
+      if (fabs(u[k]) < best) {
+        best = fabs(u[k]);
+        ax = k;
+      }
+    const double ui = u[ax];
+    for (int k = 0; k < 3; ++k) wt[k] = (k == ax ? 1.0 : 0.0) - ui * u[k];
+    nw = sqrt(dot3(wt, wt));
+  }
+  for (int k = 0; k < 3; ++k) w[k] = wt[k] / nw;
+  cross3(w, u, v);
+  // reverse
+  double gwt_in[3], gu[3], tmp[3];
+  cross3(u, gv, tmp);  // d e / d w from v = w x u
+  for (int k = 0; k < 3; ++k) gwt_in[k] = gw[k] + tmp[k];
+  cross3(gv, w, gu);   // d e / d u from v = w x u
+  const double gww = dot3(gwt_in, w);
+  double gwt[3];
+  for (int k = 0; k < 3; ++k) gwt[k] = (gwt_in[k] - gww * w[k]) / nw;
+  const double gwu = dot3(gwt, u);
+  if (ax < 0) {
+    for (int k = 0; k < 3; ++k) {
+      gup[k] = gwt[k] - gwu * u[k];
+      gu[k] -= gwu * rr[k] + ru * gwt[k];
+    }
+  } else {
+    const double ui = u[ax];
+    for (int k = 0; k < 3; ++k) {
+      gup[k] = 0.0;
+      gu[k] -= ui * gwt[k];
+    }
+    gu[ax] -= gwu;
+  }
+  const double guu = dot3(gu, u);
+  for (int k = 0; k < 3; ++k) {
+    const double gd = (gu[k] - guu * u[k]) / nd;
+    gCb[k] = gd;
+    gCa[k] = -gd;
+  }
+  return true;
+}
+
 }  // namespace
 
 __host__ __device__ ViewRec setup_view(const double* P, const double* motion, int W, int H) {
@@ -430,43 +495,45 @@ __global__ void pair_setup_kernel(int n_views, long long n_pairs, const int32_t*
 }
 
 // Gradient of one pair's e with respect to the per-view quantities the pair reads,
-// q = (C[3], up[3], cofc[9]) of view a, then of view b (30 values): the frame
-// (w, v) carries forward-mode tangents in the sources and up axes (12
-// directions); A = cofc [w v] is linear in cofc.  G = d e / d A as for pair_grad.
+// q = (C[3], up[3], cofc[9]) of view a, then of view b (30 values), from
+// G = d e / d A (the pair kernel's adjoint): A = cofc [w v] is linear in cofc, and
+// the frame (w, v) is differentiated in reverse mode (pencil_frame_adjoint).
 __device__ void pair_grad_q(const PairRec& pr, const ViewRec* __restrict__ views, const double* __restrict__ G,
                             double* __restrict__ out) {
   if (pr.status != 0 || pr.nk <= 0) {
     for (int j = 0; j < 30; ++j) out[j] = 0.0;
     return;
   }
-  using D = Dual<12>;
-  const int ab[2] = {pr.a, pr.b};
-  D C[2][3], up[2][3];
-  for (int s = 0; s < 2; ++s) {
-    const ViewRec& vr = views[ab[s]];
-    for (int k = 0; k < 3; ++k) {
-      C[s][k] = D(vr.C[k]);
-      C[s][k].d[6 * s + k] = 1.0;
-      up[s][k] = D(vr.up[k]);
-      up[s][k].d[6 * s + 3 + k] = 1.0;
-    }
-  }
-  D w[3], v[3];
-  pencil_frame(C[0], C[1], up[0], up[1], w, v);
-  double gf[12];
-  for (int j = 0; j < 12; ++j) gf[j] = 0.0;
-  for (int s = 0; s < 2; ++s) {
-    const double* cof = views[ab[s]].cofc;
+  const ViewRec& va = views[pr.a];
+  const ViewRec& vb = views[pr.b];
+  const ViewRec* vv[2] = {&va, &vb};
+  // d e / d w and d e / d v through A = cofc [w v]
+  double gw[3] = {0.0, 0.0, 0.0}, gv[3] = {0.0, 0.0, 0.0};
+  for (int s = 0; s < 2; ++s)
     for (int i = 0; i < 3; ++i) {
       const double g0 = G[6 * s + 2 * i], g1 = G[6 * s + 2 * i + 1];
-      for (int k = 0; k < 3; ++k) out[15 * s + 6 + 3 * i + k] = g0 * w[k].v + g1 * v[k].v;
-      for (int j = 0; j < 12; ++j)
-        gf[j] += g0 * (cof[3 * i] * w[0].d[j] + cof[3 * i + 1] * w[1].d[j] + cof[3 * i + 2] * w[2].d[j]) +
-                 g1 * (cof[3 * i] * v[0].d[j] + cof[3 * i + 1] * v[1].d[j] + cof[3 * i + 2] * v[2].d[j]);
+      const double* cof = vv[s]->cofc + 3 * i;
+      for (int k = 0; k < 3; ++k) {
+        gw[k] += g0 * cof[k];
+        gv[k] += g1 * cof[k];
+      }
     }
+  double w[3], v[3], gCa[3], gCb[3], gup[3];
+  if (!pencil_frame_adjoint(va.C, vb.C, va.up, vb.up, gw, gv, w, v, gCa, gCb, gup)) {
+    for (int j = 0; j < 30; ++j) out[j] = 0.0;
+    return;
   }
   for (int s = 0; s < 2; ++s)
-    for (int k = 0; k < 6; ++k) out[15 * s + k] = gf[6 * s + k];
+    for (int i = 0; i < 3; ++i) {
+      const double g0 = G[6 * s + 2 * i], g1 = G[6 * s + 2 * i + 1];
+      for (int k = 0; k < 3; ++k) out[15 * s + 6 + 3 * i + k] = g0 * w[k] + g1 * v[k];
+    }
+  for (int k = 0; k < 3; ++k) {
+    out[k] = gCa[k];
+    out[3 + k] = gup[k];
+    out[15 + k] = gCb[k];
+    out[18 + k] = gup[k];
+  }
 }
 
 __global__ void pair_grad_q_kernel(long long n_pairs, const PairRec* __restrict__ prs,
