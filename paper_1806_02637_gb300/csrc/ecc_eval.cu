@@ -548,7 +548,7 @@ __device__ __forceinline__ double pair_warp_forward(const PairArgs& g, long long
     };
     const int n_last = K - 32 * (n_tiles - 1);  // samples of the last tile (1 .. 32)
     const LaneGeom qf = lane_geom((float)lane - 15.5f);
-    const LaneGeom ql = lane_geom((float)lane + 0.5f - 0.5f * (float)n_last);
+    const float jj_last = (float)lane + 0.5f - 0.5f * (float)n_last;  // the ragged tile's offsets
     const float tan_half_tile = tanf(15.5f * dkf);
     const int r0lo = pr.r0lo, r1lo = pr.r1lo;
     const unsigned len0 = (unsigned)max(pr.r0hi - pr.r0lo, 0), len1 = (unsigned)max(pr.r1hi - pr.r1lo, 0);
@@ -590,8 +590,8 @@ __device__ __forceinline__ double pair_warp_forward(const PairArgs& g, long long
       if (tfull < tmax) {  // the ragged last tile
         const int k = 32 * (t0 + tfull) + lane;
         const bool valid = k < K && ((unsigned)(k - r0lo) < len0 || (unsigned)(k - r1lo) < len1);
-        const float dd = tile_diff<T>(recw + 8 * tfull, recw + 8 * (16 + tfull), ql, sa, sb, sca, scb, n_alpha,
-                                      n_s, inv_dalpha, inv_ds_f);
+        const float dd = tile_diff<T>(recw + 8 * tfull, recw + 8 * (16 + tfull), lane_geom(jj_last), sa, sb, sca,
+                                      scb, n_alpha, n_s, inv_dalpha, inv_ds_f);
         acc += valid ? dd * dd : 0.0f;
       }
       __syncwarp();  // records are rewritten by the next chunk
@@ -763,7 +763,7 @@ __device__ __forceinline__ double pair_warp_adjoint(const PairArgs& g, long long
     };
     const int n_last = K - 32 * (n_tiles - 1);
     const LaneGeom qf = lane_geom((float)lane - 15.5f);
-    const LaneGeom ql = lane_geom((float)lane + 0.5f - 0.5f * (float)n_last);
+    const float jj_last = (float)lane + 0.5f - 0.5f * (float)n_last;  // the ragged tile's offsets
     const float tan_half_tile = tanf(15.5f * dkf);
     const int r0lo = pr.r0lo, r1lo = pr.r1lo;
     const unsigned len0 = (unsigned)max(pr.r0hi - pr.r0lo, 0), len1 = (unsigned)max(pr.r1hi - pr.r1lo, 0);
@@ -808,7 +808,8 @@ __device__ __forceinline__ double pair_warp_adjoint(const PairArgs& g, long long
       }
       if (tfull < tmax) {
         const int k = 32 * (t0 + tfull) + lane;
-        one_tile(t0 + tfull, ql, k < K && ((unsigned)(k - r0lo) < len0 || (unsigned)(k - r1lo) < len1));
+        one_tile(t0 + tfull, lane_geom(jj_last),
+                 k < K && ((unsigned)(k - r0lo) < len0 || (unsigned)(k - r1lo) < len1));
       }
       __syncwarp();
     }

@@ -2,6 +2,7 @@
 
     python -m paper_1806_02637_gb300.profile_case --case radon  [--views 32]
     python -m paper_1806_02637_gb300.profile_case --case pairs  [--views 128]
+    python -m paper_1806_02637_gb300.profile_case --case grad   [--views 128]
 
 Each case builds a seeded subset of the 496-view short scan (620 x 480 detector,
 768 x 768 dRadon/ds grid, 512 kappa), runs the call three times untimed and three
@@ -19,7 +20,7 @@ import numpy as np
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", choices=["radon", "pairs"], required=True)
+    ap.add_argument("--case", choices=["radon", "pairs", "grad"], required=True)
     ap.add_argument("--views", type=int, default=0, help="views of the short scan (default 32 / 128)")
     a = ap.parse_args(argv)
     import torch
@@ -31,7 +32,7 @@ def main(argv=None) -> int:
     if a.case == "radon":
         n = a.views or 32
         views = np.arange(0, cfg.n_views, 15)[:n]
-    else:
+    else:  # pairs, grad
         n = a.views or 128
         views = np.arange(0, cfg.n_views, max(1, cfg.n_views // n))[:n]
     sc = synth.make_scan(cfg, views=views)
@@ -39,13 +40,20 @@ def main(argv=None) -> int:
     P = torch.from_numpy(sc["P"]).cuda()
     im = torch.from_numpy(sc["images"]).cuda()
 
+    # the gradient case: seeded rigid motion, rotations N(0, 1 deg), translations N(0, 2 mm)
+    rng = np.random.default_rng(2024)
+    motion = torch.from_numpy(np.concatenate([rng.normal(0.0, np.deg2rad(1.0), (len(views), 3)),
+                                              rng.normal(0.0, 2.0, (len(views), 3))], axis=1)).cuda()
+
     def run():
         if a.case == "radon":
             return ecc.ecc_precompute_radon_derivative(ctx, P, im, cfg.n_alpha, cfg.n_s)
+        if a.case == "grad":
+            return ecc.ecc_evaluate_grad(ctx, P, S, cfg.W, cfg.H, cfg.K, motion=motion)
         return ecc.ecc_evaluate(ctx, P, S, cfg.W, cfg.H, cfg.K)
 
     S, _ = ecc.ecc_precompute_radon_derivative(ctx, P, im, cfg.n_alpha, cfg.n_s)
-    if a.case == "pairs":
+    if a.case in ("pairs", "grad"):
         del im
     torch.cuda.synchronize()
     for _ in range(3):
