@@ -23,6 +23,7 @@ namespace ecc {
 namespace {
 
 constexpr int kWarpsPerBlock = 8;
+constexpr int kPairsPerForwardBlock = 2 * kWarpsPerBlock;  // the forward kernel: two pairs per warp
 
 template <typename T>
 struct Elem;
@@ -64,7 +65,13 @@ __device__ __forceinline__ float bilinear(const T* __restrict__ sv, int n_alpha,
 }
 
 constexpr int kSer = 10;           // terms of the per-tile series
-constexpr float kSerLimit = 0.1f;  // series used while |zeta| tan(15.5 dk) <= this
+constexpr float kSerLimit = 0.1f;  // series used while |zeta| tan(half tile) <= this
+// The s index advances by gh jj + gl jj per sample offset jj; gh keeps few enough
+// significant bits that gh jj is exact in FP32: 18 for the adjoint's 32-sample tiles
+// (2 jj an integer below 2^5), 16 for the forward's 64-sample tiles (4 jj an integer
+// below 2^8).
+constexpr unsigned kGhMask32 = 0xffffffc0u;
+constexpr unsigned kGhMask64 = 0xffffff00u;
 
 // Per (tile, view) anchor record, 32 floats (128 B), written by one lane and read by
 // the whole warp through shared memory.  The fields of the series path come first.
@@ -109,7 +116,7 @@ __device__ __forceinline__ Anchor load_anchor(const float4* __restrict__ src) {
 // pipes; A, c and the row directions arrive split into (hi, lo) pairs.
 __device__ Anchor make_anchor(const float* __restrict__ Adf, float4 c, const float4* __restrict__ alpha_dir,
                               int n_alpha, float inv_dalpha, df inv_ds, df half_ns1, float inv_ds_f, df dk,
-                              float tan_half_tile) {
+                              float tan_half_tile, unsigned gh_mask) {
   const df cx = {c.x, c.z}, cy = {c.y, c.w};
   const df A0 = {Adf[0], Adf[1]}, A1 = {Adf[2], Adf[3]}, A2 = {Adf[4], Adf[5]};
   const df A3 = {Adf[6], Adf[7]}, A4 = {Adf[8], Adf[9]}, A5 = {Adf[10], Adf[11]};
@@ -171,7 +178,7 @@ __device__ Anchor make_anchor(const float* __restrict__ Adf, float4 c, const flo
   const df ih = df_rsqrt(df_add(df_mul(l0, l0), df_mul(l1, l1)));
   const df t1 = df_add(df_mul(l0, p0), df_mul(l1, p1));
   const df g = df_mul(df_mul(df_mul(ih, df_sub(df_mul(df_mul(l2, t1), df_mul(ih, ih)), p2)), dk), inv_ds);
-  const float gh = __int_as_float(__float_as_int(g.hi) & (int)0xffffffc0);
+  const float gh = __int_as_float((int)((unsigned)__float_as_int(g.hi) & gh_mask));
   r.gh = gh;
   r.gl = (g.hi - gh) + g.lo;
   // Series over the tile in t = tan(delta).  In the anchor frame the normal of the
@@ -369,7 +376,11 @@ __device__ __forceinline__ float sample_grad(const T* __restrict__ sv, int n_alp
 
 // ------------------------------------------------------------ forward fast path
 //
-// The forward kernel evaluates a tile with the anchors' own number of series terms
+// The forward kernel takes tiles of 64 samples: each lane evaluates samples lane and
+// lane + 32 of a tile from the tile's one anchor per view, so an anchor serves twice
+// the samples of the 32-sample tiles of the adjoint, and one anchor pass (one anchor
+// per lane) covers eight tiles of two pairs, which a warp evaluates one after the
+// other.  A tile is evaluated with the anchors' own number of series terms
 // (warp-uniform), without per-sample clamps and with two-row gathers at 32-bit
 // indices.  A tile in which some lane's alpha row is outside [0, n_alpha - 2] (the
 // fold at alpha = pi and the wrap of the last row) or in which a view needs the
@@ -377,13 +388,29 @@ __device__ __forceinline__ float sample_grad(const T* __restrict__ sv, int n_alp
 // are bitwise those of the general code (zero coefficients beyond the anchor's
 // terms leave its Horner chains unchanged).
 
-// Per-lane constants of one tile shape (full tiles, or the ragged last tile).
+// Per-lane constants of one tile shape (adjoint: full tiles, or the ragged last tile).
 struct LaneGeom {
   float jj, de, t, t2, tmd, cd, sd;
 };
 
-template <int NT>
-__device__ __forceinline__ void series_position(const float4* __restrict__ rec, const LaneGeom& q, unsigned& mu,
+// Forward per-lane constants of one sample offset jj (sample steps from the anchor):
+// t = tan(jj dk), t^2 and tan(jj dk) - jj dk.  The general code derives the rest.
+struct LaneT {
+  float jj, t, t2, tmd;
+};
+
+__device__ __forceinline__ LaneT lane_t(float jj, float dkf) {
+  LaneT q;
+  q.jj = jj;
+  const float de = jj * dkf;
+  q.t = tanf(de);
+  q.t2 = q.t * q.t;
+  q.tmd = tan_minus_angle(de, q.t);
+  return q;
+}
+
+template <int NT, class Q>
+__device__ __forceinline__ void series_position(const float4* __restrict__ rec, const Q& q, unsigned& mu,
                                                 int& n, float& fa, float& fs) {
   const float4 h0 = rec[0], h1 = rec[1];
   const float* __restrict__ c = reinterpret_cast<const float*>(rec + 2);  // dco[kSer], sco[kSer]
@@ -423,31 +450,36 @@ __device__ __forceinline__ float bilinear_rows(const T* __restrict__ sv, int n_s
   return fmaf(fa, v1 - v0, v0);
 }
 
-// Difference S_a - S_b of this lane's sample by the general per-sample code.
+// Difference S_a - S_b of one sample (offset jj from the anchors) by the general
+// per-sample code: either evaluation, any alpha row (the fold and the wrap included).
 template <typename T>
-__device__ __noinline__ float tile_diff_general(const float4* __restrict__ ra, const float4* __restrict__ rb,
-                                               const LaneGeom& q, const T* __restrict__ sa,
-                                               const T* __restrict__ sb, float sca, float scb, int n_alpha,
-                                               int n_s, float inv_dalpha, float inv_ds_f) {
+__device__ __noinline__ float sample_diff_general(const float4* __restrict__ ra, const float4* __restrict__ rb,
+                                                  float jj, float t, float tmd, float dkf, const T* __restrict__ sa,
+                                                  const T* __restrict__ sb, float sca, float scb, int n_alpha,
+                                                  int n_s, float inv_dalpha, float inv_ds_f) {
+  const float de = jj * dkf;
+  float sd, cd;
+  sincosf(de, &sd, &cd);
   Loc la, lb;
   {
     const Anchor an = load_anchor(ra);
-    la = an.ser != 0.0f ? locate_series(an, q.t, q.tmd, q.jj, n_alpha, n_s)
-                        : locate(an, q.cd, q.sd, q.jj, q.de, n_alpha, n_s, inv_dalpha, inv_ds_f);
+    la = an.ser != 0.0f ? locate_series(an, t, tmd, jj, n_alpha, n_s)
+                        : locate(an, cd, sd, jj, de, n_alpha, n_s, inv_dalpha, inv_ds_f);
   }
   {
     const Anchor an = load_anchor(rb);
-    lb = an.ser != 0.0f ? locate_series(an, q.t, q.tmd, q.jj, n_alpha, n_s)
-                        : locate(an, q.cd, q.sd, q.jj, q.de, n_alpha, n_s, inv_dalpha, inv_ds_f);
+    lb = an.ser != 0.0f ? locate_series(an, t, tmd, jj, n_alpha, n_s)
+                        : locate(an, cd, sd, jj, de, n_alpha, n_s, inv_dalpha, inv_ds_f);
   }
   return sca * sample(sa, n_alpha, n_s, la) - scb * sample(sb, n_alpha, n_s, lb);
 }
 
+// One sample per lane (a last tile of at most 32 samples).
 template <typename T, int NT>
-__device__ __forceinline__ float tile_diff_series(const float4* __restrict__ ra, const float4* __restrict__ rb,
-                                                 const LaneGeom& q, const T* __restrict__ sa,
-                                                 const T* __restrict__ sb, float sca, float scb, int n_alpha,
-                                                 int n_s, float inv_dalpha, float inv_ds_f) {
+__device__ __forceinline__ float sample_diff_series(const float4* __restrict__ ra, const float4* __restrict__ rb,
+                                                   const LaneT& q, float dkf, const T* __restrict__ sa,
+                                                   const T* __restrict__ sb, float sca, float scb, int n_alpha,
+                                                   int n_s, float inv_dalpha, float inv_ds_f) {
   unsigned ma, mb;
   int na, nb;
   float faa, fsa, fab, fsb;
@@ -455,159 +487,202 @@ __device__ __forceinline__ float tile_diff_series(const float4* __restrict__ ra,
   series_position<NT>(rb, q, mb, nb, fab, fsb);
   const unsigned last = (unsigned)(n_alpha - 1);
   if (__any_sync(0xffffffffu, ma >= last || mb >= last))  // fold or last-row wrap somewhere in the tile
-    return tile_diff_general<T>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f);
+    return sample_diff_general<T>(ra, rb, q.jj, q.t, q.tmd, dkf, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha,
+                                  inv_ds_f);
   const float ga = sca * ra[1].x, gb = scb * rb[1].x;  // storage scale times the anchor's fold
   return ga * bilinear_rows(sa, n_s, ma, na, faa, fsa) - gb * bilinear_rows(sb, n_s, mb, nb, fab, fsb);
 }
 
-// Two consecutive full tiles at once (twice the gathers in flight per warp).
+template <typename T>
+__device__ __forceinline__ float sample_diff(const float4* __restrict__ ra, const float4* __restrict__ rb,
+                                            const LaneT& q, float dkf, const T* __restrict__ sa,
+                                            const T* __restrict__ sb, float sca, float scb, int n_alpha, int n_s,
+                                            float inv_dalpha, float inv_ds_f) {
+  const float na = ra[1].w, nb = rb[1].w;  // terms of the two anchors (warp-uniform)
+  if (na == 0.0f || nb == 0.0f)
+    return sample_diff_general<T>(ra, rb, q.jj, q.t, q.tmd, dkf, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha,
+                                  inv_ds_f);
+  const float nt = fmaxf(na, nb);
+#define ECC_ONE(NT_) \
+  return sample_diff_series<T, NT_>(ra, rb, q, dkf, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f)
+  if (nt <= 3.0f) ECC_ONE(3);
+  if (nt <= 4.0f) ECC_ONE(4);
+  if (nt <= 6.0f) ECC_ONE(6);
+  if (nt <= 8.0f) ECC_ONE(8);
+  ECC_ONE(kSer);
+#undef ECC_ONE
+}
+
+// Both samples of every lane in a tile (offsets q0 and q1 from the same anchors).
 template <typename T, int NT>
-__device__ __forceinline__ bool tile_diff2_series(const float4* __restrict__ ra0, const float4* __restrict__ rb0,
-                                                  const float4* __restrict__ ra1, const float4* __restrict__ rb1,
-                                                  const LaneGeom& q, const T* __restrict__ sa,
-                                                  const T* __restrict__ sb, float sca, float scb, int n_alpha,
-                                                  int n_s, float& d0, float& d1) {
+__device__ __forceinline__ bool tile_diff_series(const float4* __restrict__ ra, const float4* __restrict__ rb,
+                                                 const LaneT& q0, const LaneT& q1, const T* __restrict__ sa,
+                                                 const T* __restrict__ sb, float sca, float scb, int n_alpha,
+                                                 int n_s, float& d0, float& d1) {
   unsigned ma0, mb0, ma1, mb1;
   int na0, nb0, na1, nb1;
   float fa0, fs0, fb0, gs0, fa1, fs1, fb1, gs1;
-  series_position<NT>(ra0, q, ma0, na0, fa0, fs0);
-  series_position<NT>(rb0, q, mb0, nb0, fb0, gs0);
-  series_position<NT>(ra1, q, ma1, na1, fa1, fs1);
-  series_position<NT>(rb1, q, mb1, nb1, fb1, gs1);
+  series_position<NT>(ra, q0, ma0, na0, fa0, fs0);
+  series_position<NT>(ra, q1, ma1, na1, fa1, fs1);
+  series_position<NT>(rb, q0, mb0, nb0, fb0, gs0);
+  series_position<NT>(rb, q1, mb1, nb1, fb1, gs1);
   const unsigned last = (unsigned)(n_alpha - 1);
   if (__any_sync(0xffffffffu, ma0 >= last || mb0 >= last || ma1 >= last || mb1 >= last)) return false;
-  const float ga0 = sca * ra0[1].x, gb0 = scb * rb0[1].x, ga1 = sca * ra1[1].x, gb1 = scb * rb1[1].x;
+  const float ga = sca * ra[1].x, gb = scb * rb[1].x;
   const float A0 = bilinear_rows(sa, n_s, ma0, na0, fa0, fs0), B0 = bilinear_rows(sb, n_s, mb0, nb0, fb0, gs0);
   const float A1 = bilinear_rows(sa, n_s, ma1, na1, fa1, fs1), B1 = bilinear_rows(sb, n_s, mb1, nb1, fb1, gs1);
-  d0 = ga0 * A0 - gb0 * B0;
-  d1 = ga1 * A1 - gb1 * B1;
+  d0 = ga * A0 - gb * B0;
+  d1 = ga * A1 - gb * B1;
   return true;
 }
 
 template <typename T>
-__device__ __forceinline__ bool tile_diff2(const float4* __restrict__ ra0, const float4* __restrict__ rb0,
-                                           const float4* __restrict__ ra1, const float4* __restrict__ rb1,
-                                           const LaneGeom& q, const T* __restrict__ sa, const T* __restrict__ sb,
-                                           float sca, float scb, int n_alpha, int n_s, float& d0, float& d1) {
-  const float n0 = fminf(fminf(ra0[1].w, rb0[1].w), fminf(ra1[1].w, rb1[1].w));
-  if (n0 == 0.0f) return false;
-  const float nt = fmaxf(fmaxf(ra0[1].w, rb0[1].w), fmaxf(ra1[1].w, rb1[1].w));
-  if (nt <= 3.0f) return tile_diff2_series<T, 3>(ra0, rb0, ra1, rb1, q, sa, sb, sca, scb, n_alpha, n_s, d0, d1);
-  if (nt <= 4.0f) return tile_diff2_series<T, 4>(ra0, rb0, ra1, rb1, q, sa, sb, sca, scb, n_alpha, n_s, d0, d1);
-  if (nt <= 6.0f) return tile_diff2_series<T, 6>(ra0, rb0, ra1, rb1, q, sa, sb, sca, scb, n_alpha, n_s, d0, d1);
-  if (nt <= 8.0f) return tile_diff2_series<T, 8>(ra0, rb0, ra1, rb1, q, sa, sb, sca, scb, n_alpha, n_s, d0, d1);
-  return tile_diff2_series<T, kSer>(ra0, rb0, ra1, rb1, q, sa, sb, sca, scb, n_alpha, n_s, d0, d1);
-}
-
-template <typename T>
-__device__ __forceinline__ float tile_diff(const float4* __restrict__ ra, const float4* __restrict__ rb,
-                                          const LaneGeom& q, const T* __restrict__ sa, const T* __restrict__ sb,
-                                          float sca, float scb, int n_alpha, int n_s, float inv_dalpha,
-                                          float inv_ds_f) {
+__device__ __forceinline__ void tile_diff(const float4* __restrict__ ra, const float4* __restrict__ rb,
+                                          const LaneT& q0, const LaneT& q1, float dkf, const T* __restrict__ sa,
+                                          const T* __restrict__ sb, float sca, float scb, int n_alpha, int n_s,
+                                          float inv_dalpha, float inv_ds_f, float& d0, float& d1) {
   const float na = ra[1].w, nb = rb[1].w;  // terms of the two anchors (warp-uniform)
-  if (na == 0.0f || nb == 0.0f)
-    return tile_diff_general<T>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f);
-  const float nt = fmaxf(na, nb);
-  if (nt <= 3.0f) return tile_diff_series<T, 3>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f);
-  if (nt <= 4.0f) return tile_diff_series<T, 4>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f);
-  if (nt <= 6.0f) return tile_diff_series<T, 6>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f);
-  if (nt <= 8.0f) return tile_diff_series<T, 8>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f);
-  return tile_diff_series<T, kSer>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f);
+  bool done = false;
+  if (na != 0.0f && nb != 0.0f) {
+    const float nt = fmaxf(na, nb);
+#define ECC_TWO(NT_) tile_diff_series<T, NT_>(ra, rb, q0, q1, sa, sb, sca, scb, n_alpha, n_s, d0, d1)
+    if (nt <= 3.0f)
+      done = ECC_TWO(3);
+    else if (nt <= 4.0f)
+      done = ECC_TWO(4);
+    else if (nt <= 5.0f)
+      done = ECC_TWO(5);
+    else if (nt <= 6.0f)
+      done = ECC_TWO(6);
+    else if (nt <= 8.0f)
+      done = ECC_TWO(8);
+    else
+      done = ECC_TWO(kSer);
+#undef ECC_TWO
+  }
+  if (!done) {
+    d0 = sample_diff_general<T>(ra, rb, q0.jj, q0.t, q0.tmd, dkf, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha,
+                                inv_ds_f);
+    d1 = sample_diff_general<T>(ra, rb, q1.jj, q1.t, q1.tmd, dkf, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha,
+                                inv_ds_f);
+  }
 }
 
-// Forward value of pair p on one warp (one plane per lane, tiles of 32): d (Eq. 15), the
-// Cauchy e (Eq. 16) and N_kappa.
+// Forward values of pairs p0 and p0 + 1 on one warp: d (Eq. 15), the Cauchy e
+// (Eq. 16) and N_kappa of each; returns the sum of their e.  Tiles of 64 samples; the
+// anchor pass takes lane = 16 (pair) + 8 (view) + tile, eight tiles of both pairs.
+// A tile's anchor sits at the sum of its two 32-sample centre directions, which is
+// the direction of their mean angle (the anchor depends on the direction only, not
+// on its length): the tile's centre for full tiles; for a last tile of 33..63
+// samples the mean of the two centres, within 31.5 steps of each of its samples.  A
+// last tile of at most 32 samples is its own 32-sample tile.
 template <typename T>
-__device__ __forceinline__ double pair_warp_forward(const PairArgs& g, long long p, int lane,
-                                                    float4* __restrict__ recw) {
-  const PairRec& pr = g.prs[p];
-  const int nk = pr.status == 0 ? pr.nk : 0;
+__device__ __forceinline__ double pair_warp2_forward(const PairArgs& g, long long p0, int lane,
+                                                     float4* __restrict__ recw) {
+  const bool has1 = p0 + 1 < g.n_pairs;
+  const long long p1 = has1 ? p0 + 1 : p0;
   const int n_tiles = g.n_tiles, n_alpha = g.n_alpha, n_s = g.n_s, K = g.K;
-  float acc = 0.0f;
-  if (nk > 0) {
+  const int n_t64 = (K + 63) / 64;         // tiles of 64 samples (n_tiles counts those of 32)
+  const int n_rem = K - 64 * (n_t64 - 1);  // samples of the last one (1 .. 64)
+  const int nk0 = g.prs[p0].status == 0 ? g.prs[p0].nk : 0;
+  const int nk1 = has1 && g.prs[p1].status == 0 ? g.prs[p1].nk : 0;
+  const float inv_dalpha = g.inv_dalpha, inv_ds_f = g.inv_ds_f;
+  float acc0 = 0.0f, acc1 = 0.0f;
+  if (nk0 > 0 || nk1 > 0) {
     const T* __restrict__ sino = static_cast<const T*>(g.sino);
     const size_t vstride = (size_t)n_alpha * n_s;
-    const T* __restrict__ sa = sino + (size_t)pr.a * vstride;
-    const T* __restrict__ sb = sino + (size_t)pr.b * vstride;
-    const float sca = g.scales ? g.scales[pr.a] : 1.0f;
-    const float scb = g.scales ? g.scales[pr.b] : 1.0f;
-    const float inv_dalpha = g.inv_dalpha, inv_ds_f = g.inv_ds_f;
-    const df inv_ds = {g.inv_ds_hi, g.inv_ds_lo};
-    const df half_ns1 = {g.half_hi, g.half_lo};
-    const float dkf = pr.dk_hi;
-    const df dk = {pr.dk_hi, pr.dk_lo};
-    auto lane_geom = [&](float jj) {
-      LaneGeom q;
-      q.jj = jj;
-      q.de = jj * dkf;
-      sincosf(q.de, &q.sd, &q.cd);
-      q.t = tanf(q.de);
-      q.t2 = q.t * q.t;
-      q.tmd = tan_minus_angle(q.de, q.t);
-      return q;
-    };
-    const int n_last = K - 32 * (n_tiles - 1);  // samples of the last tile (1 .. 32)
-    const LaneGeom qf = lane_geom((float)lane - 15.5f);
-    const float jj_last = (float)lane + 0.5f - 0.5f * (float)n_last;  // the ragged tile's offsets
-    const float tan_half_tile = tanf(15.5f * dkf);
-    const int r0lo = pr.r0lo, r1lo = pr.r1lo;
-    const unsigned len0 = (unsigned)max(pr.r0hi - pr.r0lo, 0), len1 = (unsigned)max(pr.r1hi - pr.r1lo, 0);
-    const float4* __restrict__ ct = g.ctile + p * n_tiles;
-    for (int t0 = 0; t0 < n_tiles; t0 += 16) {
+    for (int t0 = 0; t0 < n_t64; t0 += 8) {
       {
-        const int v = lane >> 4;
-        int t = t0 + (lane & 15);
-        if (t >= n_tiles) t = n_tiles - 1;
-        store_anchor(recw + 8 * lane, make_anchor(pr.Af[v], ct[t], g.alpha_dir, n_alpha, inv_dalpha, inv_ds,
-                                                  half_ns1, inv_ds_f, dk, tan_half_tile));
+        const long long p = (lane >> 4) ? p1 : p0;
+        const PairRec& pr = g.prs[p];
+        const int v = (lane >> 3) & 1;
+        const int u = min(t0 + (lane & 7), n_t64 - 1);
+        const float4* __restrict__ ct = g.ctile + p * n_tiles;
+        float4 c = ct[2 * u];
+        if (2 * u + 1 < n_tiles) {
+          const float4 cb = ct[2 * u + 1];
+          const df x = df_add(df{c.x, c.z}, df{cb.x, cb.z}), y = df_add(df{c.y, c.w}, df{cb.y, cb.w});
+          c = make_float4(x.hi, y.hi, x.lo, y.lo);
+        }
+        const df inv_ds = {g.inv_ds_hi, g.inv_ds_lo};
+        const df half_ns1 = {g.half_hi, g.half_lo};
+        const df dk = {pr.dk_hi, pr.dk_lo};
+        store_anchor(recw + 8 * lane, make_anchor(pr.Af[v], c, g.alpha_dir, n_alpha, inv_dalpha, inv_ds, half_ns1,
+                                                  inv_ds_f, dk, tanf(31.5f * pr.dk_hi), kGhMask64));
       }
       __syncwarp();
-      const int tmax = min(16, n_tiles - t0);
-      const int tfull = (t0 + tmax == n_tiles && n_last != 32) ? tmax - 1 : tmax;
-      int tt = 0;
-      for (; tt + 1 < tfull; tt += 2) {
-        const int k = 32 * (t0 + tt) + lane;
-        const bool v0 = (unsigned)(k - r0lo) < len0 || (unsigned)(k - r1lo) < len1;
-        const bool v1 = (unsigned)(k + 32 - r0lo) < len0 || (unsigned)(k + 32 - r1lo) < len1;
-        float d0, d1;
-        if (!tile_diff2<T>(recw + 8 * tt, recw + 8 * (16 + tt), recw + 8 * (tt + 1), recw + 8 * (17 + tt), qf, sa,
-                           sb, sca, scb, n_alpha, n_s, d0, d1)) {
-          d0 = tile_diff<T>(recw + 8 * tt, recw + 8 * (16 + tt), qf, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha,
-                            inv_ds_f);
-          d1 = tile_diff<T>(recw + 8 * (tt + 1), recw + 8 * (17 + tt), qf, sa, sb, sca, scb, n_alpha, n_s,
-                            inv_dalpha, inv_ds_f);
+      const int umax = min(8, n_t64 - t0);
+      const int ufull = (t0 + umax == n_t64 && n_rem != 64) ? umax - 1 : umax;
+#pragma unroll 1
+      for (int ps = 0; ps < 2; ++ps) {
+        if ((ps ? nk1 : nk0) == 0) continue;  // warp-uniform
+        const PairRec& pr = g.prs[ps ? p1 : p0];
+        const T* __restrict__ sa = sino + (size_t)pr.a * vstride;
+        const T* __restrict__ sb = sino + (size_t)pr.b * vstride;
+        const float sca = g.scales ? g.scales[pr.a] : 1.0f;
+        const float scb = g.scales ? g.scales[pr.b] : 1.0f;
+        const float dkf = pr.dk_hi;
+        const int r0lo = pr.r0lo, r1lo = pr.r1lo;
+        const unsigned len0 = (unsigned)max(pr.r0hi - pr.r0lo, 0), len1 = (unsigned)max(pr.r1hi - pr.r1lo, 0);
+        auto valid = [&](int k) { return (unsigned)(k - r0lo) < len0 || (unsigned)(k - r1lo) < len1; };
+        const float4* __restrict__ rw = recw + 8 * 16 * ps;  // view a: tiles 0..7, view b: tiles 8..15
+        float acc = 0.0f;
+        if (ufull > 0) {
+          const LaneT q0 = lane_t((float)lane - 31.5f, dkf), q1 = lane_t((float)lane + 0.5f, dkf);
+          for (int uu = 0; uu < ufull; ++uu) {
+            const int k = 64 * (t0 + uu) + lane;
+            float d0, d1;
+            tile_diff<T>(rw + 8 * uu, rw + 8 * (8 + uu), q0, q1, dkf, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha,
+                         inv_ds_f, d0, d1);
+            acc += valid(k) ? d0 * d0 : 0.0f;
+            acc += valid(k + 32) ? d1 * d1 : 0.0f;
+          }
         }
-        acc += v0 ? d0 * d0 : 0.0f;
-        acc += v1 ? d1 * d1 : 0.0f;
-      }
-      for (; tt < tfull; ++tt) {
-        const int k = 32 * (t0 + tt) + lane;
-        const bool valid = (unsigned)(k - r0lo) < len0 || (unsigned)(k - r1lo) < len1;
-        const float dd = tile_diff<T>(recw + 8 * tt, recw + 8 * (16 + tt), qf, sa, sb, sca, scb, n_alpha, n_s,
-                                      inv_dalpha, inv_ds_f);
-        acc += valid ? dd * dd : 0.0f;
-      }
-      if (tfull < tmax) {  // the ragged last tile
-        const int k = 32 * (t0 + tfull) + lane;
-        const bool valid = k < K && ((unsigned)(k - r0lo) < len0 || (unsigned)(k - r1lo) < len1);
-        const float dd = tile_diff<T>(recw + 8 * tfull, recw + 8 * (16 + tfull), lane_geom(jj_last), sa, sb, sca,
-                                      scb, n_alpha, n_s, inv_dalpha, inv_ds_f);
-        acc += valid ? dd * dd : 0.0f;
+        if (ufull < umax) {  // the ragged last tile
+          const int k = 64 * (t0 + ufull) + lane;
+          const float4* __restrict__ ra = rw + 8 * ufull;
+          const float4* __restrict__ rb = rw + 8 * (8 + ufull);
+          if (n_rem > 32) {
+            const float mid = 15.5f + 0.25f * (float)n_rem;  // anchor: mean angle of the two 32-sample centres
+            float d0, d1;
+            tile_diff<T>(ra, rb, lane_t((float)lane - mid, dkf), lane_t((float)lane + 32.0f - mid, dkf), dkf, sa, sb,
+                         sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f, d0, d1);
+            acc += valid(k) ? d0 * d0 : 0.0f;
+            acc += k + 32 < K && valid(k + 32) ? d1 * d1 : 0.0f;
+          } else {
+            const float dd = sample_diff<T>(ra, rb, lane_t((float)lane + 0.5f - 0.5f * (float)n_rem, dkf), dkf, sa,
+                                            sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f);
+            acc += k < K && valid(k) ? dd * dd : 0.0f;
+          }
+        }
+        if (ps)
+          acc1 += acc;
+        else
+          acc0 += acc;
       }
       __syncwarp();  // records are rewritten by the next chunk
     }
   }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  const float d = nk > 0 ? acc / (float)nk : 0.0f;
-  const float e = g.cauchy_c > 0.0f ? d / (1.0f + d / g.cauchy_c) : d;
-  if (lane == 0) {
-    if (g.per_pair) {
-      g.per_pair[2 * p] = (double)d;
-      g.per_pair[2 * p + 1] = (double)e;
-    }
-    if (g.nk_out) g.nk_out[p] = nk;
+  for (int o = 16; o > 0; o >>= 1) {
+    acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
+    acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
   }
-  return (double)e;
+  double e_sum = 0.0;
+  for (int ps = 0; ps < (has1 ? 2 : 1); ++ps) {
+    const long long p = ps ? p1 : p0;
+    const int nk = ps ? nk1 : nk0;
+    const float d = nk > 0 ? (ps ? acc1 : acc0) / (float)nk : 0.0f;
+    const float e = g.cauchy_c > 0.0f ? d / (1.0f + d / g.cauchy_c) : d;
+    if (lane == 0) {
+      if (g.per_pair) {
+        g.per_pair[2 * p] = (double)d;
+        g.per_pair[2 * p + 1] = (double)e;
+      }
+      if (g.nk_out) g.nk_out[p] = nk;
+    }
+    e_sum += (double)e;
+  }
+  return e_sum;
 }
 
 // ------------------------------------------------------------ adjoint fast path
@@ -797,7 +872,7 @@ __device__ __forceinline__ double pair_warp_adjoint(const PairArgs& g, long long
         int t = t0 + (lane & 15);
         if (t >= n_tiles) t = n_tiles - 1;
         store_anchor(recw + 8 * lane, make_anchor(pr.Af[v], ct[t], g.alpha_dir, n_alpha, inv_dalpha, inv_ds,
-                                                  half_ns1, inv_ds_f, dk, tan_half_tile));
+                                                  half_ns1, inv_ds_f, dk, tan_half_tile, kGhMask32));
       }
       __syncwarp();
       const int tmax = min(16, n_tiles - t0);
@@ -835,16 +910,19 @@ __device__ __forceinline__ double pair_warp_adjoint(const PairArgs& g, long long
   return (double)e;
 }
 
-// One block of kWarpsPerBlock consecutive pairs: their e summed in a fixed order
-// into partial[blk].
+// One block of consecutive pairs (kWarpsPerBlock for the adjoint, two per warp for the
+// forward kernel): their e summed in a fixed order into partial[blk].
 template <typename T, bool GRAD, bool SERVE = false>
 __device__ __forceinline__ void pair_block(const PairArgs& g, long long blk, double* e_warp, float4* recs) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const long long p = blk * kWarpsPerBlock + wib;
+  float4* recw = recs + (size_t)wib * 32 * 8;
   double e_val = 0.0;
-  if (p < g.n_pairs) {  // warp-uniform
-    float4* recw = recs + (size_t)wib * 32 * 8;
-    e_val = GRAD ? pair_warp_adjoint<T, !SERVE>(g, p, lane, recw) : pair_warp_forward<T>(g, p, lane, recw);
+  if (GRAD) {
+    const long long p = blk * kWarpsPerBlock + wib;
+    if (p < g.n_pairs) e_val = pair_warp_adjoint<T, !SERVE>(g, p, lane, recw);  // warp-uniform
+  } else {
+    const long long p = blk * kPairsPerForwardBlock + 2 * wib;
+    if (p < g.n_pairs) e_val = pair_warp2_forward<T>(g, p, lane, recw);  // warp-uniform
   }
   if (lane == 0) e_warp[wib] = e_val;
   __syncthreads();
@@ -935,7 +1013,8 @@ cudaError_t launch_ecc_pairs(long long n_pairs, const PairRec* prs, const float4
                              int n_alpha, int n_s, int K, int W, int H, double cauchy_c, double* per_pair,
                              int32_t* nk_out, double* block_partial, double* Gpp, int* n_blocks_out,
                              const LaunchHooks& hooks, cudaStream_t stream) {
-  const long long nb = (n_pairs + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const long long ppb = Gpp ? kWarpsPerBlock : kPairsPerForwardBlock;
+  const long long nb = (n_pairs + ppb - 1) / ppb;
   *n_blocks_out = (int)nb;
   if (nb == 0) return cudaSuccess;
   const dim3 grid((unsigned)nb), block(kWarpsPerBlock * 32);
