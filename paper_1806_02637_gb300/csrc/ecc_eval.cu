@@ -24,6 +24,7 @@ namespace {
 
 constexpr int kWarpsPerBlock = 8;
 constexpr int kPairsPerForwardBlock = 2 * kWarpsPerBlock;  // the forward kernel: two pairs per warp
+constexpr int kForwardWavesForTwo = 3;  // ... when that leaves at least this many waves of blocks
 
 template <typename T>
 struct Elem;
@@ -64,8 +65,13 @@ __device__ __forceinline__ float bilinear(const T* __restrict__ sv, int n_alpha,
   return fmaf(fa, v1 - v0, v0);
 }
 
-constexpr int kSer = 10;           // terms of the per-tile series
-constexpr float kSerLimit = 0.1f;  // series used while |zeta| tan(half tile) <= this
+constexpr int kSer = 16;  // terms of the per-tile series (at most)
+// The series is used while rho = |zeta| tan(half tile) is at most this (else the closed
+// form per sample): 0.2 for the forward's 64-sample tiles (up to 16 terms: the tail
+// after them stays below 1e-8 bins), 0.1 for the adjoint's 32-sample tiles (up to 10
+// terms), whose rho is half as large.
+constexpr float kSerLimit64 = 0.2f;
+constexpr float kSerLimit32 = 0.1f;
 // The s index advances by gh jj + gl jj per sample offset jj; gh keeps few enough
 // significant bits that gh jj is exact in FP32: 18 for the adjoint's 32-sample tiles
 // (2 jj an integer below 2^5), 16 for the forward's 64-sample tiles (4 jj an integer
@@ -73,7 +79,7 @@ constexpr float kSerLimit = 0.1f;  // series used while |zeta| tan(half tile) <=
 constexpr unsigned kGhMask32 = 0xffffffc0u;
 constexpr unsigned kGhMask64 = 0xffffff00u;
 
-// Per (tile, view) anchor record, 32 floats (128 B), written by one lane and read by
+// Per (tile, view) anchor record, 44 floats (176 B), written by one lane and read by
 // the whole warp through shared memory.  The fields of the series path come first.
 struct Anchor {
   int m0, n0;      // alpha row and s bin of the tile-centre line
@@ -86,24 +92,25 @@ struct Anchor {
   float a, b;      // zeta = a + i b: rate of the normal direction in the anchor frame
   float p3, s0;    // rate of the offset, anchor offset s [px]
 };
-static_assert(sizeof(Anchor) == 128, "anchor record is 32 floats");
+static_assert(sizeof(Anchor) == 176, "anchor record is 44 floats");
+constexpr int kRec = sizeof(Anchor) / sizeof(float4);  // float4 words per record
 
 union AnchorVec {
   Anchor a;
-  float4 v[8];
+  float4 v[kRec];
 };
 
 __device__ __forceinline__ void store_anchor(float4* __restrict__ dst, const Anchor& x) {
   AnchorVec u;
   u.a = x;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) dst[i] = u.v[i];
+  for (int i = 0; i < kRec; ++i) dst[i] = u.v[i];
 }
 
 __device__ __forceinline__ Anchor load_anchor(const float4* __restrict__ src) {
   AnchorVec u;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) u.v[i] = src[i];
+  for (int i = 0; i < kRec; ++i) u.v[i] = src[i];
   return u.a;
 }
 
@@ -116,7 +123,7 @@ __device__ __forceinline__ Anchor load_anchor(const float4* __restrict__ src) {
 // pipes; A, c and the row directions arrive split into (hi, lo) pairs.
 __device__ Anchor make_anchor(const float* __restrict__ Adf, float4 c, const float4* __restrict__ alpha_dir,
                               int n_alpha, float inv_dalpha, df inv_ds, df half_ns1, float inv_ds_f, df dk,
-                              float tan_half_tile, unsigned gh_mask) {
+                              float tan_half_tile, unsigned gh_mask, float ser_limit, int max_terms) {
   const df cx = {c.x, c.z}, cy = {c.y, c.w};
   const df A0 = {Adf[0], Adf[1]}, A1 = {Adf[2], Adf[3]}, A2 = {Adf[4], Adf[5]};
   const df A3 = {Adf[6], Adf[7]}, A4 = {Adf[8], Adf[9]}, A5 = {Adf[10], Adf[11]};
@@ -187,22 +194,22 @@ __device__ Anchor make_anchor(const float* __restrict__ Adf, float4 c, const flo
   //   s(t) = (s0 - p3 t) / |1 + zeta t| = (s0 - p3 t) sum_k e_k t^k,
   // where (1 + 2 a t + |zeta|^2 t^2)^(-1/2) = sum_k e_k t^k is the Legendre generating
   // function: e_0 = 1, e_1 = -a, (k + 1) e_(k+1) = -((2k + 1) a e_k + k |zeta|^2 e_(k-1)).
-  // With |zeta t| <= 0.1 the truncation after t^10 is below 1e-10 of the offsets.
+  // With |zeta t| <= 0.2 the truncation after t^16 is below 1e-11 of the offsets.
   const float zr = r.a, zi = r.b;
   const float z2 = fmaf(zr, zr, zi * zi);
   // Terms needed: with rho = |zeta| tan(half tile) the k-th terms are bounded by
   // rho^k inv_dalpha (alpha) and (|s0| rho^k + |p3| t rho^(k-1)) inv_ds (s), since
   // |Im zeta^k| <= |zeta|^k and |e_k| <= |zeta|^k; the tails after n terms are these
-  // geometric sums.  The smallest n >= 2 whose tail bound is below 1e-8 bins is kept
-  // (the s index carries ~6e-8 bins of FP32 rounding anyway).
+  // geometric sums.  The smallest n >= 2 whose tail bound is below 1e-8 bins is kept,
+  // at most max_terms (the s index carries ~6e-8 bins of FP32 rounding anyway).
   const float rho = sqrtf(z2) * tan_half_tile;
   int nser = 0;
-  if (rho <= kSerLimit && isfinite(r.s0) && isfinite(r.fs0) && isfinite(r.fa0)) {
+  if (rho <= ser_limit && isfinite(r.s0) && isfinite(r.fs0) && isfinite(r.fa0)) {
     const float cs = fabsf(r.s0) * inv_ds_f, cp = fabsf(r.p3) * tan_half_tile * inv_ds_f;
     const float inv1m = 1.0f / (1.0f - rho);
     float rn = rho * rho;  // rho^n for n = 2
     nser = 2;
-    while (nser < kSer && ((inv_dalpha + cs) * rn * rho + cp * rn) * inv1m > 1e-8f) {
+    while (nser < max_terms && ((inv_dalpha + cs) * rn * rho + cp * rn) * inv1m > 1e-8f) {
       rn *= rho;
       ++nser;
     }
@@ -509,6 +516,7 @@ __device__ __forceinline__ float sample_diff(const float4* __restrict__ ra, cons
   if (nt <= 4.0f) ECC_ONE(4);
   if (nt <= 6.0f) ECC_ONE(6);
   if (nt <= 8.0f) ECC_ONE(8);
+  if (nt <= 12.0f) ECC_ONE(12);
   ECC_ONE(kSer);
 #undef ECC_ONE
 }
@@ -550,12 +558,12 @@ __device__ __forceinline__ void tile_diff(const float4* __restrict__ ra, const f
       done = ECC_TWO(3);
     else if (nt <= 4.0f)
       done = ECC_TWO(4);
-    else if (nt <= 5.0f)
-      done = ECC_TWO(5);
     else if (nt <= 6.0f)
       done = ECC_TWO(6);
     else if (nt <= 8.0f)
       done = ECC_TWO(8);
+    else if (nt <= 12.0f)
+      done = ECC_TWO(12);
     else
       done = ECC_TWO(kSer);
 #undef ECC_TWO
@@ -568,7 +576,7 @@ __device__ __forceinline__ void tile_diff(const float4* __restrict__ ra, const f
   }
 }
 
-// Forward values of pairs p0 and p0 + 1 on one warp: d (Eq. 15), the Cauchy e
+// Forward values of pairs p0 and (if has1) p1 on one warp: d (Eq. 15), the Cauchy e
 // (Eq. 16) and N_kappa of each; returns the sum of their e.  Tiles of 64 samples; the
 // anchor pass takes lane = 16 (pair) + 8 (view) + tile, eight tiles of both pairs.
 // A tile's anchor sits at the sum of its two 32-sample centre directions, which is
@@ -577,10 +585,9 @@ __device__ __forceinline__ void tile_diff(const float4* __restrict__ ra, const f
 // samples the mean of the two centres, within 31.5 steps of each of its samples.  A
 // last tile of at most 32 samples is its own 32-sample tile.
 template <typename T>
-__device__ __forceinline__ double pair_warp2_forward(const PairArgs& g, long long p0, int lane,
-                                                     float4* __restrict__ recw) {
-  const bool has1 = p0 + 1 < g.n_pairs;
-  const long long p1 = has1 ? p0 + 1 : p0;
+__device__ __forceinline__ double pair_warp2_forward(const PairArgs& g, long long p0, long long p1, bool has1,
+                                                     int lane, float4* __restrict__ recw) {
+  if (!has1) p1 = p0;  // the second half of the anchor pass repeats the first pair
   const int n_tiles = g.n_tiles, n_alpha = g.n_alpha, n_s = g.n_s, K = g.K;
   const int n_t64 = (K + 63) / 64;         // tiles of 64 samples (n_tiles counts those of 32)
   const int n_rem = K - 64 * (n_t64 - 1);  // samples of the last one (1 .. 64)
@@ -607,8 +614,8 @@ __device__ __forceinline__ double pair_warp2_forward(const PairArgs& g, long lon
         const df inv_ds = {g.inv_ds_hi, g.inv_ds_lo};
         const df half_ns1 = {g.half_hi, g.half_lo};
         const df dk = {pr.dk_hi, pr.dk_lo};
-        store_anchor(recw + 8 * lane, make_anchor(pr.Af[v], c, g.alpha_dir, n_alpha, inv_dalpha, inv_ds, half_ns1,
-                                                  inv_ds_f, dk, tanf(31.5f * pr.dk_hi), kGhMask64));
+        store_anchor(recw + kRec * lane, make_anchor(pr.Af[v], c, g.alpha_dir, n_alpha, inv_dalpha, inv_ds, half_ns1,
+                                                  inv_ds_f, dk, tanf(31.5f * pr.dk_hi), kGhMask64, kSerLimit64, kSer));
       }
       __syncwarp();
       const int umax = min(8, n_t64 - t0);
@@ -622,37 +629,42 @@ __device__ __forceinline__ double pair_warp2_forward(const PairArgs& g, long lon
         const float sca = g.scales ? g.scales[pr.a] : 1.0f;
         const float scb = g.scales ? g.scales[pr.b] : 1.0f;
         const float dkf = pr.dk_hi;
-        const int r0lo = pr.r0lo, r1lo = pr.r1lo;
-        const unsigned len0 = (unsigned)max(pr.r0hi - pr.r0lo, 0), len1 = (unsigned)max(pr.r1hi - pr.r1lo, 0);
-        auto valid = [&](int k) { return (unsigned)(k - r0lo) < len0 || (unsigned)(k - r1lo) < len1; };
-        const float4* __restrict__ rw = recw + 8 * 16 * ps;  // view a: tiles 0..7, view b: tiles 8..15
+        unsigned vm = 0;  // bit 2 uu + h: sample 64 (t0 + uu) + 32 h + lane is valid
+        {
+          const int r0lo = pr.r0lo, r1lo = pr.r1lo;
+          const unsigned len0 = (unsigned)max(pr.r0hi - pr.r0lo, 0), len1 = (unsigned)max(pr.r1hi - pr.r1lo, 0);
+#pragma unroll
+          for (int bit = 0; bit < 16; ++bit) {
+            const int k = 64 * t0 + 32 * bit + lane;
+            if (k < K && ((unsigned)(k - r0lo) < len0 || (unsigned)(k - r1lo) < len1)) vm |= 1u << bit;
+          }
+        }
+        const float4* __restrict__ rw = recw + kRec * 16 * ps;  // view a: tiles 0..7, view b: tiles 8..15
         float acc = 0.0f;
         if (ufull > 0) {
           const LaneT q0 = lane_t((float)lane - 31.5f, dkf), q1 = lane_t((float)lane + 0.5f, dkf);
           for (int uu = 0; uu < ufull; ++uu) {
-            const int k = 64 * (t0 + uu) + lane;
             float d0, d1;
-            tile_diff<T>(rw + 8 * uu, rw + 8 * (8 + uu), q0, q1, dkf, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha,
+            tile_diff<T>(rw + kRec * uu, rw + kRec * (8 + uu), q0, q1, dkf, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha,
                          inv_ds_f, d0, d1);
-            acc += valid(k) ? d0 * d0 : 0.0f;
-            acc += valid(k + 32) ? d1 * d1 : 0.0f;
+            acc += (vm >> (2 * uu)) & 1u ? d0 * d0 : 0.0f;
+            acc += (vm >> (2 * uu + 1)) & 1u ? d1 * d1 : 0.0f;
           }
         }
         if (ufull < umax) {  // the ragged last tile
-          const int k = 64 * (t0 + ufull) + lane;
-          const float4* __restrict__ ra = rw + 8 * ufull;
-          const float4* __restrict__ rb = rw + 8 * (8 + ufull);
+          const float4* __restrict__ ra = rw + kRec * ufull;
+          const float4* __restrict__ rb = rw + kRec * (8 + ufull);
           if (n_rem > 32) {
             const float mid = 15.5f + 0.25f * (float)n_rem;  // anchor: mean angle of the two 32-sample centres
             float d0, d1;
             tile_diff<T>(ra, rb, lane_t((float)lane - mid, dkf), lane_t((float)lane + 32.0f - mid, dkf), dkf, sa, sb,
                          sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f, d0, d1);
-            acc += valid(k) ? d0 * d0 : 0.0f;
-            acc += k + 32 < K && valid(k + 32) ? d1 * d1 : 0.0f;
+            acc += (vm >> (2 * ufull)) & 1u ? d0 * d0 : 0.0f;
+            acc += (vm >> (2 * ufull + 1)) & 1u ? d1 * d1 : 0.0f;
           } else {
             const float dd = sample_diff<T>(ra, rb, lane_t((float)lane + 0.5f - 0.5f * (float)n_rem, dkf), dkf, sa,
                                             sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f);
-            acc += k < K && valid(k) ? dd * dd : 0.0f;
+            acc += (vm >> (2 * ufull)) & 1u ? dd * dd : 0.0f;
           }
         }
         if (ps)
@@ -794,6 +806,7 @@ __device__ __forceinline__ float tile_adjoint(const float4* __restrict__ ra, con
   if (nt <= 4.0f) ECC_ADJ(4);
   if (nt <= 6.0f) ECC_ADJ(6);
   if (nt <= 8.0f) ECC_ADJ(8);
+  if (nt <= 12.0f) ECC_ADJ(12);
   ECC_ADJ(kSer);
 #undef ECC_ADJ
 }
@@ -852,9 +865,9 @@ __device__ __forceinline__ double pair_warp_adjoint(const PairArgs& g, long long
       float ga[3], gb[3];
       const int tt = t & 15;
       const float dd =
-          FAST ? tile_adjoint<T>(recw + 8 * tt, recw + 8 * (16 + tt), q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha,
+          FAST ? tile_adjoint<T>(recw + kRec * tt, recw + kRec * (16 + tt), q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha,
                                  inv_ds_f, Af, ckx, cky, ga, gb)
-               : tile_adjoint_general_body<T>(recw + 8 * tt, recw + 8 * (16 + tt), q, sa, sb, sca, scb, n_alpha,
+               : tile_adjoint_general_body<T>(recw + kRec * tt, recw + kRec * (16 + tt), q, sa, sb, sca, scb, n_alpha,
                                               n_s, inv_dalpha, inv_ds_f, Af, ckx, cky, ga, gb);
       acc += valid ? dd * dd : 0.0f;
       const float w2 = valid ? 2.0f * dd : 0.0f;
@@ -871,8 +884,8 @@ __device__ __forceinline__ double pair_warp_adjoint(const PairArgs& g, long long
         const int v = lane >> 4;
         int t = t0 + (lane & 15);
         if (t >= n_tiles) t = n_tiles - 1;
-        store_anchor(recw + 8 * lane, make_anchor(pr.Af[v], ct[t], g.alpha_dir, n_alpha, inv_dalpha, inv_ds,
-                                                  half_ns1, inv_ds_f, dk, tan_half_tile, kGhMask32));
+        store_anchor(recw + kRec * lane, make_anchor(pr.Af[v], ct[t], g.alpha_dir, n_alpha, inv_dalpha, inv_ds,
+                                                  half_ns1, inv_ds_f, dk, tan_half_tile, kGhMask32, kSerLimit32, 10));
       }
       __syncwarp();
       const int tmax = min(16, n_tiles - t0);
@@ -915,14 +928,18 @@ __device__ __forceinline__ double pair_warp_adjoint(const PairArgs& g, long long
 template <typename T, bool GRAD, bool SERVE = false>
 __device__ __forceinline__ void pair_block(const PairArgs& g, long long blk, double* e_warp, float4* recs) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  float4* recw = recs + (size_t)wib * 32 * 8;
+  float4* recw = recs + (size_t)wib * 32 * kRec;
   double e_val = 0.0;
   if (GRAD) {
     const long long p = blk * kWarpsPerBlock + wib;
     if (p < g.n_pairs) e_val = pair_warp_adjoint<T, !SERVE>(g, p, lane, recw);  // warp-uniform
   } else {
-    const long long p = blk * kPairsPerForwardBlock + 2 * wib;
-    if (p < g.n_pairs) e_val = pair_warp2_forward<T>(g, p, lane, recw);  // warp-uniform
+    // two pairs per warp (blk 2W + w and blk 2W + W + w, W warps: the block's warps run
+    // neighbouring pairs side by side) when the launch has fewer blocks than pairs / W
+    const bool two = (long long)gridDim.x * kWarpsPerBlock < g.n_pairs;
+    const long long p = blk * (two ? kPairsPerForwardBlock : kWarpsPerBlock) + wib;
+    if (p < g.n_pairs)  // warp-uniform
+      e_val = pair_warp2_forward<T>(g, p, p + kWarpsPerBlock, two && p + kWarpsPerBlock < g.n_pairs, lane, recw);
   }
   if (lane == 0) e_warp[wib] = e_val;
   __syncthreads();
@@ -939,7 +956,7 @@ __device__ __forceinline__ void pair_block(const PairArgs& g, long long blk, dou
 template <typename T, bool GRAD>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, GRAD ? 3 : 4) ecc_pair_kernel(PairArgs g) {
   __shared__ double e_warp[kWarpsPerBlock];
-  __shared__ float4 recs[kWarpsPerBlock * 32 * 8];  // anchor records, 4 KB per warp
+  __shared__ float4 recs[kWarpsPerBlock * 32 * kRec];  // anchor records, 5.5 KB per warp
   pair_block<T, GRAD>(g, blockIdx.x, e_warp, recs);
 }
 
@@ -974,7 +991,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 3) serve_pair_kernel(cons
                                                                          int n_jobs,
                                                                          unsigned long long* __restrict__ next) {
   __shared__ double e_warp[kWarpsPerBlock];
-  __shared__ float4 recs[kWarpsPerBlock * 32 * 8];  // anchor records, 4 KB per warp
+  __shared__ float4 recs[kWarpsPerBlock * 32 * kRec];  // anchor records, 5.5 KB per warp
   __shared__ long long item;
   const long long total = boff[n_jobs];
   for (;;) {
@@ -1013,7 +1030,13 @@ cudaError_t launch_ecc_pairs(long long n_pairs, const PairRec* prs, const float4
                              int n_alpha, int n_s, int K, int W, int H, double cauchy_c, double* per_pair,
                              int32_t* nk_out, double* block_partial, double* Gpp, int* n_blocks_out,
                              const LaunchHooks& hooks, cudaStream_t stream) {
-  const long long ppb = Gpp ? kWarpsPerBlock : kPairsPerForwardBlock;
+  // The forward kernel takes two pairs per warp when that still leaves several waves of
+  // blocks (the anchor pass then serves both); smaller launches keep one per warp.
+  int dev = 0, n_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    n_sm = 1;
+  const bool two = !Gpp && n_pairs >= (long long)kPairsPerForwardBlock * 4 * n_sm * kForwardWavesForTwo;
+  const long long ppb = two ? kPairsPerForwardBlock : kWarpsPerBlock;
   const long long nb = (n_pairs + ppb - 1) / ppb;
   *n_blocks_out = (int)nb;
   if (nb == 0) return cudaSuccess;
