@@ -49,6 +49,7 @@ struct ecc_ctx {
   int samp_views = 0, samp_pairs = 0, samp_K = 0, samp_W = 0, samp_H = 0;
   const void* samp_pair_ptr = nullptr;
   Buf h_P, h_img, h_sino, h_total;  // buffers of the host-buffer entry point
+  cudaStream_t copy_stream = nullptr;  // its image uploads, per precompute batch
   ecc_serve* serve = nullptr;       // serving scheduler, created by the first ecc_submit
 };
 
@@ -157,15 +158,24 @@ int check_geometry_args(ecc_ctx* c, int n_views, const void* P, int W, int H, in
 }
 
 
+// Views per dRadon/ds batch: the weighted images of a batch take at most 256 MiB.
+int radon_batch_views(int n_views, int W, int H, int n_s) {
+  const size_t plane = ecc::radon_plane_bytes(W, H, n_s);
+  const size_t max_batch_bytes = (size_t)256 << 20;
+  return (int)std::max<size_t>(1, std::min<size_t>((size_t)n_views, max_batch_bytes / plane));
+}
+
+// batch_ready (or NULL): one event per batch, which the stream waits for before the
+// batch reads its images.
 int run_precompute(ecc_ctx* c, int n_views, const double* P, const float* images, int W, int H, int n_alpha, int n_s,
-                   int dtype, void* sino_out, float* scales_out, cudaStream_t s) {
+                   int dtype, void* sino_out, float* scales_out, cudaStream_t s,
+                   const cudaEvent_t* batch_ready = nullptr) {
   int rc;
   if ((rc = ensure(c, c->views, sizeof(ecc::ViewRec) * (size_t)n_views, "views")) != ECC_OK) return rc;
   const size_t tbytes = sizeof(ecc::RadonRow) * (size_t)n_views * n_alpha + sizeof(ecc::RadonView) * (size_t)n_views;
   if ((rc = ensure(c, c->rtable, tbytes, "radon table")) != ECC_OK) return rc;
   const size_t plane = ecc::radon_plane_bytes(W, H, n_s);
-  const size_t max_batch_bytes = (size_t)256 << 20;
-  int batch = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_views, max_batch_bytes / plane));
+  const int batch = radon_batch_views(n_views, W, H, n_s);
   if ((rc = ensure(c, c->wimg, plane * (size_t)batch, "weighted images")) != ECC_OK) return rc;
   if (dtype == ECC_F16 &&
       (rc = ensure(c, c->stage, ecc::radon_f16_stage_bytes(n_alpha, n_s, batch), "FP16 staging")) != ECC_OK)
@@ -178,7 +188,8 @@ int run_precompute(ecc_ctx* c, int n_views, const double* P, const float* images
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "view set-up launch");
   e = ecc::launch_radon((const ecc::ViewRec*)c->views.p, n_views, images, W, H, n_alpha, n_s, dtype, sino_out,
-                        scales_out, (ecc::RadonRow*)c->rtable.p, c->wimg.p, (float*)c->stage.p, batch, hk, s);
+                        scales_out, (ecc::RadonRow*)c->rtable.p, c->wimg.p, (float*)c->stage.p, batch, hk, s,
+                        batch_ready);
   if (e != cudaSuccess) return cuda_fail(c, e, "radon launch");
   return ECC_OK;
 }
@@ -344,6 +355,7 @@ void ecc_destroy(ecc_ctx* c) {
     if (r.e) cudaEventDestroy(r.e);
   }
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   delete c;
 }
 
@@ -513,10 +525,46 @@ int ecc_scan_consistency_host(ecc_ctx* c, int n_views, const double* P_host, con
   if ((rc = ensure(c, c->h_sino, sb, "host-call sinograms")) != ECC_OK) return rc;
   if ((rc = ensure(c, c->h_total, sizeof(double), "host-call total")) != ECC_OK) return rc;
   cudaError_t e = cudaMemcpyAsync(c->h_P.p, P_host, pb, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(c->h_img.p, images_host, ib, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
+  // From pinned host memory the images go up per precompute batch on a second stream,
+  // so that the upload of batch b + 1 overlaps the projection of batch b; pageable
+  // memory (whose asynchronous copies block the host) is copied in one piece.
+  const int batch = radon_batch_views(n_views, W, H, n_s);
+  const int n_batches = (n_views + batch - 1) / batch;
+  cudaPointerAttributes pa;
+  const bool pinned = cudaPointerGetAttributes(&pa, images_host) == cudaSuccess && pa.type == cudaMemoryTypeHost;
+  (void)cudaGetLastError();  // a pageable pointer may leave an error from the query
+  struct Events {
+    std::vector<cudaEvent_t> ev;
+    ~Events() {
+      for (cudaEvent_t x : ev) cudaEventDestroy(x);
+    }
+  } ready;
+  if (pinned && n_batches > 1) {
+    if (!c->copy_stream && (e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(c, e, "copy stream");
+    for (int b = 0; b <= n_batches && e == cudaSuccess; ++b) {  // [n_batches]: the start marker
+      cudaEvent_t x;
+      e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+      if (e == cudaSuccess) ready.ev.push_back(x);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "upload events");
+    // the uploads follow all earlier work of the stream (earlier calls read these buffers)
+    e = cudaEventRecord(ready.ev[n_batches], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->copy_stream, ready.ev[n_batches], 0);
+    for (int b = 0; b < n_batches && e == cudaSuccess; ++b) {
+      const size_t v0 = (size_t)b * batch, nv = (size_t)std::min(batch, n_views - b * batch);
+      const size_t px = (size_t)W * H;
+      e = cudaMemcpyAsync((float*)c->h_img.p + v0 * px, images_host + v0 * px, sizeof(float) * px * nv,
+                          cudaMemcpyHostToDevice, c->copy_stream);
+      if (e == cudaSuccess) e = cudaEventRecord(ready.ev[b], c->copy_stream);
+    }
+  } else {
+    e = cudaMemcpyAsync(c->h_img.p, images_host, ib, cudaMemcpyHostToDevice, s);
+  }
   if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
   rc = run_precompute(c, n_views, (const double*)c->h_P.p, (const float*)c->h_img.p, W, H, n_alpha, n_s, ECC_F32,
-                      c->h_sino.p, nullptr, s);
+                      c->h_sino.p, nullptr, s, ready.ev.empty() ? nullptr : ready.ev.data());
   if (rc != ECC_OK) return rc;
   rc = run_evaluate(c, n_views, (const double*)c->h_P.p, nullptr, c->h_sino.p, nullptr, W, H, n_alpha, n_s, ECC_F32,
                     n_kappa, cauchy_c, nullptr, (int)np, (double*)c->h_total.p, nullptr, nullptr, nullptr, nullptr, false,

@@ -89,7 +89,8 @@ inline void pair_args_grid(PairArgs& g, int n_alpha, int n_s, int W, int H) {
 // Launchers (return cudaError_t of the launch).
 cudaError_t launch_radon(const ViewRec* views, int n_views, const float* images, int W, int H, int n_alpha, int n_s,
                          int dtype, void* sino_out, float* scales_out, RadonRow* table, void* wimg, float* stage,
-                         int batch_views, const LaunchHooks& hooks, cudaStream_t stream);
+                         int batch_views, const LaunchHooks& hooks, cudaStream_t stream,
+                         const cudaEvent_t* batch_ready = nullptr);  // per batch: wait before reading its images
 size_t radon_f16_stage_bytes(int n_alpha, int n_s, int batch_views);
 int radon_pad(int W, int H, int n_s);
 // Bytes of one view's weighted-image planes (interpolation pairs, both orientations).

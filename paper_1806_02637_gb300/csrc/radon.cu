@@ -255,20 +255,25 @@ __global__ void __launch_bounds__(32 * kAlphaPerBlock) joseph_kernel(const Radon
 }
 
 // FP16 storage: per-view scale = max|S| / 2^14 (1 if the view is all zero), so
-// every stored value is in FP16's normal range; stored = S / scale.
-__global__ void __launch_bounds__(256) absmax_scale_kernel(const float* __restrict__ s32, size_t per_view,
-                                                          float* __restrict__ scales) {
-  __shared__ float sh[256];
-  const float* p = s32 + (size_t)blockIdx.x * per_view;
+// every stored value is in FP16's normal range; stored = S / scale.  The max of a view
+// is split over gridDim.x blocks, each folding its part into the view's slot by an
+// atomic max on the bit pattern (non-negative floats order as their bits); the slots
+// start at zero and scale_finalize_kernel turns them into scales in place.
+__global__ void __launch_bounds__(256) absmax_kernel(const float* __restrict__ s32, size_t per_view,
+                                                     unsigned* __restrict__ max_bits) {
+  const float* __restrict__ p = s32 + (size_t)blockIdx.y * per_view;
+  const size_t chunk = (per_view + gridDim.x - 1) / gridDim.x;
+  const size_t beg = (size_t)blockIdx.x * chunk;
+  const size_t end = beg + chunk < per_view ? beg + chunk : per_view;
   float m = 0.0f;
-  for (size_t i = threadIdx.x; i < per_view; i += blockDim.x) m = fmaxf(m, fabsf(p[i]));
-  sh[threadIdx.x] = m;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sh[threadIdx.x] = fmaxf(sh[threadIdx.x], sh[threadIdx.x + w]);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) scales[blockIdx.x] = sh[0] > 0.0f ? sh[0] / 16384.0f : 1.0f;
+  for (size_t i = beg + threadIdx.x; i < end; i += blockDim.x) m = fmaxf(m, fabsf(p[i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(max_bits + blockIdx.y, __float_as_uint(m));
+}
+
+__global__ void scale_finalize_kernel(float* __restrict__ scales, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) scales[i] = scales[i] > 0.0f ? scales[i] / 16384.0f : 1.0f;
 }
 
 __global__ void quantize_f16_kernel(const float* __restrict__ s32, size_t per_view, size_t n,
@@ -299,7 +304,8 @@ size_t radon_f16_stage_bytes(int n_alpha, int n_s, int batch_views) {
 
 cudaError_t launch_radon(const ViewRec* views, int n_views, const float* images, int W, int H, int n_alpha, int n_s,
                          int dtype, void* sino_out, float* scales_out, RadonRow* table, void* wimg,
-                         float* stage, int batch_views, const LaunchHooks& hooks, cudaStream_t stream) {
+                         float* stage, int batch_views, const LaunchHooks& hooks, cudaStream_t stream,
+                         const cudaEvent_t* batch_ready) {
   // table and per-view weights (RadonView array sits right after the table)
   RadonView* rv = reinterpret_cast<RadonView*>(table + (size_t)n_views * n_alpha);
   {
@@ -331,6 +337,7 @@ cudaError_t launch_radon(const ViewRec* views, int n_views, const float* images,
       e = cudaMemsetAsync(wimg, 0, sizeof(float2) * jg.plane * nb, stream);
       if (e != cudaSuccess) return e;
     }
+    if (batch_ready && (e = cudaStreamWaitEvent(stream, batch_ready[v0 / batch_views], 0)) != cudaSuccess) return e;
     hooks.on_begin("weight_kernel", stream);
     weight_kernel<<<dim3((W + 32) / 32, (H + 32) / 32, nb), dim3(32, 8), 0, stream>>>(
         images + (size_t)v0 * W * H, rv + v0, W, H, jg.pad, jg.pitch_r, jg.pitch_c, wv, jg.plane);
@@ -352,9 +359,14 @@ cudaError_t launch_radon(const ViewRec* views, int n_views, const float* images,
     if (e != cudaSuccess) return e;
     if (dtype == 1) {
       const size_t per_view = (size_t)n_alpha * n_s;
-      hooks.on_begin("absmax_scale_kernel", stream);
-      absmax_scale_kernel<<<nb, 256, 0, stream>>>(stage, per_view, scales_out + v0);
-      hooks.on_end("absmax_scale_kernel", stream);
+      e = cudaMemsetAsync(scales_out + v0, 0, sizeof(float) * nb, stream);
+      if (e != cudaSuccess) return e;
+      const unsigned per_block = 256 * 16;  // 16 elements per thread, at most 64 blocks per view
+      const unsigned bpv = (unsigned)std::min<size_t>(64, (per_view + per_block - 1) / per_block);
+      hooks.on_begin("absmax_kernel", stream);
+      absmax_kernel<<<dim3(bpv, nb), 256, 0, stream>>>(stage, per_view, reinterpret_cast<unsigned*>(scales_out + v0));
+      hooks.on_end("absmax_kernel", stream);
+      scale_finalize_kernel<<<(nb + 255) / 256, 256, 0, stream>>>(scales_out + v0, nb);
       const size_t n = per_view * nb;
       hooks.on_begin("quantize_f16_kernel", stream);
       quantize_f16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(

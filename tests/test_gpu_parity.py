@@ -204,6 +204,22 @@ def test_host_entry_matches_device_path():
     assert abs(t_host - ref) <= 1e-4 * ref
 
 
+def test_host_entry_pinned_upload_in_batches():
+    """From pinned host memory the images go up per precompute batch (47 views of c2's
+    size per batch: three here) on a second stream, overlapping the projections.  The
+    total equals the pageable call's and the device path's bitwise, call after call."""
+    ecc = _ecc()
+    cfg = synth.CONFIGS["c2"]
+    views = tuple(range(0, 496, 5))[:100]
+    sc = H.scan("c2", views)
+    pinned = torch.from_numpy(np.ascontiguousarray(sc["images"], dtype=np.float32)).pin_memory()
+    t_pinned = [ecc.ecc_scan_consistency_host(_ctx(), sc["P"], pinned, cfg.n_alpha, cfg.n_s, cfg.K) for _ in range(2)]
+    t_pageable = ecc.ecc_scan_consistency_host(_ctx(), sc["P"], sc["images"], cfg.n_alpha, cfg.n_s, cfg.K)
+    S, _ = _gpu_sino(sc, cfg.n_alpha, cfg.n_s)
+    t_dev, _, _ = _gpu_eval(sc["P"], S, cfg.W, cfg.H, cfg.K)
+    assert t_pinned[0] == t_pinned[1] == t_pageable == t_dev
+
+
 def test_deterministic_and_pair_order():
     cfg = synth.CONFIGS["c2"]
     sc = H.scan("c2", SUB)
