@@ -1,7 +1,8 @@
 // Pair x kappa gather-reduce of the epipolar consistency metric (Eq. 15-17).
 //
-// One warp owns one pair.  The pair's K sampled planes are processed in tiles of
-// 32 (one plane per lane).  For every tile and view the line of the tile centre is
+// The pair's K sampled planes are processed in tiles: of 64 planes in the forward
+// kernel (two per lane; a warp owns one or two pairs), of 32 in the adjoint (one per
+// lane; a warp owns one pair).  For every tile and view the line of the tile centre is
 // a double-float "anchor" (computed lane-parallel, one anchor per lane), split into
 // an exact (alpha row, s bin) integer part and an FP32 fraction, with the series of
 // the tile's offsets in t = tan(delta); each lane then moves from the anchor to its
