@@ -26,6 +26,10 @@ namespace {
 constexpr int kWarpsPerBlock = 8;
 constexpr int kPairsPerForwardBlock = 2 * kWarpsPerBlock;  // the forward kernel: two pairs per warp
 constexpr int kForwardWavesForTwo = 3;  // ... when that leaves at least this many waves of blocks
+// 64-sample tiles reach 31.5 dk from their anchor, dk <= pi / n_kappa; the closed form
+// needs |delta| < pi / 2.  From 96 samples on that is at most 1.03 rad; smaller n_kappa
+// take the adjoint's 32-sample tiles (15.5 dk), without its gradient output.
+constexpr int kMinKappaForward64 = 96;
 
 template <typename T>
 struct Elem;
@@ -205,7 +209,7 @@ __device__ Anchor make_anchor(const float* __restrict__ Adf, float4 c, const flo
   // at most max_terms (the s index carries ~6e-8 bins of FP32 rounding anyway).
   const float rho = sqrtf(z2) * tan_half_tile;
   int nser = 0;
-  if (rho <= ser_limit && isfinite(r.s0) && isfinite(r.fs0) && isfinite(r.fa0)) {
+  if (tan_half_tile >= 0.0f && rho <= ser_limit && isfinite(r.s0) && isfinite(r.fs0) && isfinite(r.fa0)) {
     const float cs = fabsf(r.s0) * inv_ds_f, cp = fabsf(r.p3) * tan_half_tile * inv_ds_f;
     const float inv1m = 1.0f / (1.0f - rho);
     float rn = rho * rho;  // rho^n for n = 2
@@ -918,8 +922,10 @@ __device__ __forceinline__ double pair_warp_adjoint(const PairArgs& g, long long
     // d e / d A = (de/dd) (1/N) G
     const float r = g.cauchy_c > 0.0f ? 1.0f / (1.0f + d / g.cauchy_c) : 1.0f;
     const float scale = nk > 0 ? r * r / (float)nk : 0.0f;
+    if (g.Gpp) {  // NULL: a forward evaluation through this code (small n_kappa)
 #pragma unroll
-    for (int i = 0; i < 12; ++i) g.Gpp[12 * p + i] = (double)(G[i] * scale);
+      for (int i = 0; i < 12; ++i) g.Gpp[12 * p + i] = (double)(G[i] * scale);
+    }
   }
   return (double)e;
 }
@@ -1036,7 +1042,8 @@ cudaError_t launch_ecc_pairs(long long n_pairs, const PairRec* prs, const float4
   int dev = 0, n_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     n_sm = 1;
-  const bool two = !Gpp && n_pairs >= (long long)kPairsPerForwardBlock * 4 * n_sm * kForwardWavesForTwo;
+  const bool tiles32 = Gpp || K < kMinKappaForward64;  // the adjoint kernel (32-sample tiles)
+  const bool two = !tiles32 && n_pairs >= (long long)kPairsPerForwardBlock * 4 * n_sm * kForwardWavesForTwo;
   const long long ppb = two ? kPairsPerForwardBlock : kWarpsPerBlock;
   const long long nb = (n_pairs + ppb - 1) / ppb;
   *n_blocks_out = (int)nb;
@@ -1062,7 +1069,7 @@ cudaError_t launch_ecc_pairs(long long n_pairs, const PairRec* prs, const float4
   g.Gpp = Gpp;
 #define ECC_LAUNCH(TT)                                                      \
   do {                                                                      \
-    if (Gpp)                                                                \
+    if (tiles32)                                                            \
       ecc_pair_kernel<TT, true><<<grid, block, 0, stream>>>(g);             \
     else                                                                    \
       ecc_pair_kernel<TT, false><<<grid, block, 0, stream>>>(g);            \

@@ -137,17 +137,45 @@ def test_ecc_parity_motion_cauchy_pair_list():
     _check_pairs(sc["P"], S32, cfg.W, cfg.H, cfg.K, c=c, motion=sc["motion"], pairs=pairs)
 
 
-@pytest.mark.parametrize("K", [256, 77])
-def test_ecc_full_scan_with_opposed_views(K):
-    """Full 360-degree geometry: opposed views take the full-pi arc branch (tiles cross
-    the alpha fold); K = 77 adds a ragged last tile."""
-    cfg = synth.CONFIGS["c4"]
+@functools.lru_cache(maxsize=None)
+def _opposed_case():
     views = (0, 1, 310, 619, 620, 621, 930, 1239)
     sc = H.scan("c4", views)
-    S32 = orc.radon_derivative(sc["P"], sc["images"], 256, 346).astype(np.float32)
+    return sc, orc.radon_derivative(sc["P"], sc["images"], 256, 346).astype(np.float32)
+
+
+# The evaluation takes tiles of 64 samples; the last one holds K mod 64 (or 64): 36 and 33
+# (33..63: anchored at the mean of its two 32-sample centres), 32 and 13 (at most 32: its
+# own centre), 63 (a single ragged tile), 64 (no ragged tile), 1.
+@pytest.mark.parametrize("K", [256, 77, 100, 97, 96, 64, 63, 33, 1])
+def test_ecc_full_scan_with_opposed_views(K):
+    """Full 360-degree geometry: opposed views take the full-pi arc branch (tiles cross
+    the alpha fold); K not a multiple of 64 adds a ragged last tile."""
+    cfg = synth.CONFIGS["c4"]
+    sc, S32 = _opposed_case()
     _, _, nk, ref = _check_pairs(sc["P"], S32, cfg.W, cfg.H, K)
     full = ref["arcs"][:, 2] > 3.14
     assert full.any()
+
+
+@pytest.mark.parametrize("K", [512, 100, 77])
+def test_two_pairs_per_warp_equal_one_pair_per_warp(K):
+    """A launch of at least three waves of 16-pair blocks (all 30,628 pairs of the
+    248-view scan) gives each warp two pairs; an explicit list of 4,000 of them gives
+    each warp one.  Every pair's anchors and sums are the same code either way, so
+    d, e and N_kappa agree bitwise."""
+    cfg = synth.CONFIGS["c3"]
+    sc = H.scan("c3")
+    n = len(sc["P"])
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    if n * (n - 1) // 2 < 3 * 16 * 4 * n_sm:
+        pytest.skip("this GPU needs more pairs for two pairs per warp")
+    S, _ = _gpu_sino(sc, cfg.n_alpha, cfg.n_s)
+    _, pp, nk = _gpu_eval(sc["P"], S, cfg.W, cfg.H, K)
+    sel = np.sort(np.random.default_rng(K).choice(n * (n - 1) // 2, 4000, replace=False))
+    _, pp1, nk1 = _gpu_eval(sc["P"], S, cfg.W, cfg.H, K, pairs=synth.upper_pairs(n)[sel])
+    assert np.array_equal(nk[sel], nk1)
+    assert np.array_equal(pp[sel], pp1)
 
 
 def test_full_size_launch_sampled_pairs():
