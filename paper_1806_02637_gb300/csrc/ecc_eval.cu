@@ -462,6 +462,28 @@ __device__ __forceinline__ float bilinear_rows(const T* __restrict__ sv, int n_s
   return fmaf(fa, v1 - v0, v0);
 }
 
+// The general code's Loc of a fast-path position (row mu as an unsigned sum, bin n,
+// fractions): the fold of alpha into [0, pi) applied as loc_tail applies it.  For a
+// tile in which some lane's row left [0, n_alpha - 2] (the fold at alpha = pi or the
+// wrap of the last row): the positions are those of the general code, and so are
+// the values sampled through it.
+__device__ __forceinline__ Loc loc_folded(unsigned mu, int n, float fa, float fs, float sg, int n_alpha, int n_s) {
+  Loc o;
+  o.m = (int)mu;
+  o.n = n;
+  o.fa = fa;
+  o.fs = fs;
+  o.sign = sg;
+  if (o.m >= n_alpha || o.m < 0) {  // S(alpha + pi, s) = -S(alpha, -s)
+    o.m += o.m < 0 ? n_alpha : -n_alpha;
+    o.n = n_s - 2 - o.n;
+    o.fs = 1.0f - o.fs;
+    o.sign = -o.sign;
+  }
+  o.ok = o.m >= 0 && o.m < n_alpha;  // false only for a masked sample
+  return o;
+}
+
 // Difference S_a - S_b of one sample (offset jj from the anchors) by the general
 // per-sample code: either evaluation, any alpha row (the fold and the wrap included).
 template <typename T>
@@ -499,8 +521,8 @@ __device__ __forceinline__ float sample_diff_series(const float4* __restrict__ r
   series_position<NT>(rb, q, mb, nb, fab, fsb);
   const unsigned last = (unsigned)(n_alpha - 1);
   if (__any_sync(0xffffffffu, ma >= last || mb >= last))  // fold or last-row wrap somewhere in the tile
-    return sample_diff_general<T>(ra, rb, q.jj, q.t, q.tmd, dkf, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha,
-                                  inv_ds_f);
+    return sca * sample(sa, n_alpha, n_s, loc_folded(ma, na, faa, fsa, ra[1].x, n_alpha, n_s)) -
+           scb * sample(sb, n_alpha, n_s, loc_folded(mb, nb, fab, fsb, rb[1].x, n_alpha, n_s));
   const float ga = sca * ra[1].x, gb = scb * rb[1].x;  // storage scale times the anchor's fold
   return ga * bilinear_rows(sa, n_s, ma, na, faa, fsa) - gb * bilinear_rows(sb, n_s, mb, nb, fab, fsb);
 }
@@ -540,7 +562,13 @@ __device__ __forceinline__ bool tile_diff_series(const float4* __restrict__ ra, 
   series_position<NT>(rb, q0, mb0, nb0, fb0, gs0);
   series_position<NT>(rb, q1, mb1, nb1, fb1, gs1);
   const unsigned last = (unsigned)(n_alpha - 1);
-  if (__any_sync(0xffffffffu, ma0 >= last || mb0 >= last || ma1 >= last || mb1 >= last)) return false;
+  if (__any_sync(0xffffffffu, ma0 >= last || mb0 >= last || ma1 >= last || mb1 >= last)) {
+    d0 = sca * sample(sa, n_alpha, n_s, loc_folded(ma0, na0, fa0, fs0, ra[1].x, n_alpha, n_s)) -
+         scb * sample(sb, n_alpha, n_s, loc_folded(mb0, nb0, fb0, gs0, rb[1].x, n_alpha, n_s));
+    d1 = sca * sample(sa, n_alpha, n_s, loc_folded(ma1, na1, fa1, fs1, ra[1].x, n_alpha, n_s)) -
+         scb * sample(sb, n_alpha, n_s, loc_folded(mb1, nb1, fb1, gs1, rb[1].x, n_alpha, n_s));
+    return true;
+  }
   const float ga = sca * ra[1].x, gb = scb * rb[1].x;
   const float A0 = bilinear_rows(sa, n_s, ma0, na0, fa0, fs0), B0 = bilinear_rows(sb, n_s, mb0, nb0, fb0, gs0);
   const float A1 = bilinear_rows(sa, n_s, ma1, na1, fa1, fs1), B1 = bilinear_rows(sb, n_s, mb1, nb1, fb1, gs1);
