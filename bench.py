@@ -552,8 +552,8 @@ def run_ours(args):
                      "pair_kernel_frac_of_hbm": gbs / peaks.get("hbm_gbs", 6800.0),
                      # one ncu capture of this launch (one-pass metrics, same kernel build):
                      # DRAM read + write and L2 sector bytes per launch
-                     "pair_kernel_dram_bytes_ncu": 458404864 + 23245568,
-                     "pair_kernel_l2_bytes_ncu": 83702714 * 32}
+                     "pair_kernel_dram_bytes_ncu": 446589952 + 23083776,
+                     "pair_kernel_l2_bytes_ncu": 81681858 * 32}
     adjoint = None
     if not args.no_adjoint_forms:
         adjoint = adjoint_forms(ctx, P, sino, cfg)
