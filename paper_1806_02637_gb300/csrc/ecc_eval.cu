@@ -395,10 +395,12 @@ __device__ __forceinline__ float sample_grad(const T* __restrict__ sv, int n_alp
 // other.  A tile is evaluated with the anchors' own number of series terms
 // (warp-uniform), without per-sample clamps and with two-row gathers at 32-bit
 // indices.  A tile in which some lane's alpha row is outside [0, n_alpha - 2] (the
-// fold at alpha = pi and the wrap of the last row) or in which a view needs the
-// closed form is evaluated by the general per-sample code above instead.  Positions
-// are bitwise those of the general code (zero coefficients beyond the anchor's
-// terms leave its Horner chains unchanged).
+// fold at alpha = pi and the wrap of the last row) keeps these positions and samples
+// them through the general gather with the fold applied (loc_folded); a tile in which
+// a view needs the closed form is evaluated by the general per-sample code above.
+// Positions are bitwise those of the general code (zero coefficients beyond the
+// anchor's terms leave its Horner chains unchanged).  Launches with n_kappa below 96
+// take the adjoint's kernel instead (kMinKappaForward64).
 
 // Per-lane constants of one tile shape (adjoint: full tiles, or the ragged last tile).
 struct LaneGeom {
