@@ -120,7 +120,14 @@ static int hits_at(const view_t_r* vl, const double w[3], const double v[3], con
  * four corner planes P^T (e x x_c) give four angles; the arc between two
  * consecutive corner angles is tested at its midpoint; the valid set is the
  * complement of the one gap that misses (none: all of [-pi/2, pi/2)).
- * Returns 0 and {lo, len}, or -1 for a degenerate configuration. */
+ * The lines through an epipole outside the rectangle that meet it form one
+ * interval, so in exact arithmetic at most one gap misses.  A second miss can
+ * only be a gap of (nearly) zero width: two corners on one line through the
+ * epipole (an epipole at infinity along a detector edge, as for two sources on
+ * one line parallel to the detector's columns).  That line meets the rectangle
+ * along the edge (|s| equals the bound, a hit by reading R4), but its midpoint
+ * test may round either way; so the widest missing gap is the one that misses.
+ * Returns 0 and {lo, len}. */
 static int arc_of_view(const view_t_r* vl, const view_t_r* vo, const double w[3], const double v[3],
                        const double Ca[3], int W, int H, double* lo, double* len) {
     double Xo[4] = {vo->C[0], vo->C[1], vo->C[2], 1.0};
@@ -145,20 +152,20 @@ static int arc_of_view(const view_t_r* vl, const view_t_r* vo, const double w[3]
             kap[j] = kap[j - 1];
             kap[j - 1] = t;
         }
-    int n_miss = 0, miss = -1;
+    int miss = -1;
+    double widest = -1.0;
     for (int g = 0; g < 4; ++g) {
         double a0 = kap[g], a1 = g < 3 ? kap[g + 1] : kap[0] + ORC_PI;
-        if (!hits_at(vl, w, v, Ca, 0.5 * (a0 + a1), W, H)) {
-            ++n_miss;
+        if (!hits_at(vl, w, v, Ca, 0.5 * (a0 + a1), W, H) && a1 - a0 > widest) {
+            widest = a1 - a0;
             miss = g;
         }
     }
-    if (n_miss == 0) {
+    if (miss < 0) {
         *lo = -0.5 * ORC_PI;
         *len = ORC_PI;
         return 0;
     }
-    if (n_miss > 1) return -1;
     double a0 = kap[miss], a1 = miss < 3 ? kap[miss + 1] : kap[0] + ORC_PI;
     double l0 = a1;
     while (l0 >= 0.5 * ORC_PI) l0 -= ORC_PI;

@@ -53,6 +53,11 @@ def _np_lookup(sino, W, H, l):
     sign = np.where(alpha < 0, -1.0, 1.0)
     s = np.where(alpha < 0, -s, s)
     alpha = np.where(alpha < 0, alpha + np.pi, alpha)
+    # alpha = pi (a line with l2 = +0 and l1 < 0, or -tiny + pi rounding up) folds to 0
+    top = alpha >= np.pi
+    sign = np.where(top, -sign, sign)
+    s = np.where(top, -s, s)
+    alpha = np.where(top, alpha - np.pi, alpha)
     ia = alpha * n_alpha / np.pi
     is_ = s / (np.hypot(W, H) / (n_s - 1)) + (n_s - 1) / 2
     # extend the sinogram by the wrapped row: row n_alpha = -row 0 mirrored in s
