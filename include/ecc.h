@@ -19,10 +19,14 @@
  *     stream has reached the end of the call.
  *   - Return value: ECC_OK (0) or a negative error code; on error a message is
  *     available from ecc_last_error(), no output has been written, and the
- *     context stays usable.  Errors that only the device can see (a degenerate
- *     projection matrix, coincident sources) do not fail the call: the affected
- *     pairs report N_kappa = 0, d = e = 0, and a status bit is set that
- *     ecc_status() returns.
+ *     context stays usable.  Errors that only the device can see do not fail the
+ *     call: the affected pairs report N_kappa = 0, d = e = 0 (and no gradient),
+ *     and a status bit is set that ecc_status() returns.  They are a degenerate
+ *     projection matrix (rank below 3, det M = 0, or a NaN / Inf entry, the
+ *     motion's included: ECC_STATUS_DEGENERATE_VIEW), coincident sources
+ *     (ECC_STATUS_DEGENERATE_PAIR), and a pair whose sum of squared differences
+ *     or gradient is not finite, i.e. a NaN / Inf sinogram value on its lines,
+ *     from non-finite projection images (ECC_STATUS_NONFINITE_PAIR).
  *   - A context serves one host thread at a time; calls on one context must be
  *     issued on one stream (its scratch memory is reused across calls).
  *
@@ -62,8 +66,8 @@ enum {
 
 enum { ECC_F32 = 0, ECC_F16 = 1, ECC_BF16 = 2 };
 
-/* Device status bits returned by ecc_status(). */
-enum { ECC_STATUS_DEGENERATE_VIEW = 1, ECC_STATUS_DEGENERATE_PAIR = 2 };
+/* Device status bits returned by ecc_status() (and in ecc_result.flags). */
+enum { ECC_STATUS_DEGENERATE_VIEW = 1, ECC_STATUS_DEGENERATE_PAIR = 2, ECC_STATUS_NONFINITE_PAIR = 4 };
 
 /* Library version (major * 10000 + minor * 100 + patch). */
 int ecc_version(void);
@@ -281,13 +285,17 @@ typedef struct ecc_result {
   double latency_ms;        /* ecc_submit -> results in host memory */
   size_t footprint_bytes;   /* device memory held while admitted (precompute peak) */
   long long line_pairs;     /* line-pair samples evaluated: pairs x n_kappa x (n_iters + 1) */
+  int flags;                /* ECC_STATUS_* bits the job's device work raised (0: none); the
+                               pairs they name were left out of its totals and gradients */
 } ecc_result;
 
 /* Device memory a job needs at admission (ECC_EINVAL for an invalid job). */
 int ecc_job_footprint(const ecc_job* job, size_t* bytes);
 
 /* Queues a job and returns its ticket.  ECC_EADMIT if the job can never fit the
- * serving budget; ECC_EINVAL for an invalid job. */
+ * serving budget; ECC_EINVAL for an invalid job, including a NaN / Inf entry in
+ * P, motion0 or nodes0 (checked on the host; the images are checked on the
+ * device, see ecc_result.flags). */
 int ecc_submit(ecc_ctx* ctx, const ecc_job* job, uint64_t* ticket);
 
 /* ECC_EPENDING while the job is queued or running.  Otherwise fills *out (if not
@@ -308,10 +316,12 @@ int ecc_serve_stats(ecc_ctx* ctx, long long* rounds, long long* job_rounds, int*
  * an allocation's implicit device synchronisation).  Its scratch lives in one
  * 5 MiB statically sized device array inside the library; it calls no allocator.
  *
- *   Device: the current CUDA device; all device pointers must be on it.  The first
- *   call on each device resolves the scratch array's address (cudaGetSymbolAddress
- *   with that device current) and caches it: make that first call outside any
- *   stream capture.
+ *   Device: the current CUDA device; all device pointers must be on it.  Every call
+ *   looks up the scratch array's address in the current device's context
+ *   (cudaGetSymbolAddress, a host-side lookup that allocates nothing); nothing is
+ *   cached, so a cudaDeviceReset between calls leaves later calls valid.  The first
+ *   call on a device may load the library's module: make it outside any stream
+ *   capture.
  *   Limits of the static scratch (ECC_EINVAL with a message naming the limit
  *   otherwise): n_views <= 512, n_alpha <= 4096, n_pairs <= 8192 and
  *   n_pairs * ceil(n_kappa / 32) <= 131072; the other limits are ecc_evaluate's.

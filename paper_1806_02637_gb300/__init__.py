@@ -48,7 +48,7 @@ class _Job(ctypes.Structure):
 class _Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("total_first", ctypes.c_double),
                 ("total_last", ctypes.c_double), ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
-                ("footprint_bytes", ctypes.c_size_t), ("line_pairs", ctypes.c_longlong)]
+                ("footprint_bytes", ctypes.c_size_t), ("line_pairs", ctypes.c_longlong), ("flags", ctypes.c_int)]
 
 
 class EccError(RuntimeError):
@@ -303,6 +303,10 @@ def ecc_evaluate_noalloc(P, sino, W: int, H: int, n_kappa: int, total, cauchy_c:
         _dev(per_pair, torch.float64, "per_pair", (n_pairs, 2))
     if nkappa is not None:
         _dev(nkappa, torch.int32, "nkappa", (n_pairs,))
+    for name, t in (("P", P), ("motion", motion), ("pairs", pairs), ("scales", scales), ("total", total),
+                    ("per_pair", per_pair), ("nkappa", nkappa)):
+        if t is not None and t.device != sino.device:
+            raise EccError(f"{name} is on {t.device}, sino on {sino.device}: all tensors must be on one device")
     err = ctypes.create_string_buffer(512)
     with torch.cuda.device(sino.device):
         rc = load().ecc_evaluate_noalloc(N, _ptr(P), _ptr(motion), _ptr(sino), _ptr(scales), int(W), int(H),

@@ -260,7 +260,7 @@ int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion,
   e = ecc::launch_ecc_pairs(np, (const ecc::PairRec*)c->pairs.p, (const float4*)c->ctile.p, n_tiles,
                             (const float4*)c->adir.p, sino, scales, dtype, n_alpha, n_s, n_kappa, W, H, cauchy_c,
                             per_pair, nkappa, (double*)c->partial.p, (grad || grad_P) ? (double*)c->Gpp.p : nullptr,
-                            &nb, hk, s);
+                            c->d_status, &nb, hk, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "pair kernel launch");
   e = ecc::launch_reduce((const double*)c->partial.p, nb, total, hk, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "reduce launch");

@@ -717,10 +717,14 @@ __device__ __forceinline__ double pair_warp2_forward(const PairArgs& g, long lon
   double e_sum = 0.0;
   for (int ps = 0; ps < (has1 ? 2 : 1); ++ps) {
     const long long p = ps ? p1 : p0;
-    const int nk = ps ? nk1 : nk0;
-    const float d = nk > 0 ? (ps ? acc1 : acc0) / (float)nk : 0.0f;
+    const float acc = ps ? acc1 : acc0;
+    // a non-finite sum (non-finite sinogram values) drops the pair: N_kappa = 0, d = e = 0
+    const bool finite = isfinite(acc);
+    const int nk = finite ? (ps ? nk1 : nk0) : 0;
+    const float d = nk > 0 ? acc / (float)nk : 0.0f;
     const float e = g.cauchy_c > 0.0f ? d / (1.0f + d / g.cauchy_c) : d;
     if (lane == 0) {
+      if (!finite && g.status) atomicOr(g.status, kStatusNonfinitePair);
       if (g.per_pair) {
         g.per_pair[2 * p] = (double)d;
         g.per_pair[2 * p + 1] = (double)e;
@@ -856,13 +860,13 @@ template <typename T, bool FAST>
 __device__ __forceinline__ double pair_warp_adjoint(const PairArgs& g, long long p, int lane,
                                                     float4* __restrict__ recw) {
   const PairRec& pr = g.prs[p];
-  const int nk = pr.status == 0 ? pr.nk : 0;
+  const int nk_in = pr.status == 0 ? pr.nk : 0;
   const int n_tiles = g.n_tiles, n_alpha = g.n_alpha, n_s = g.n_s, K = g.K;
   float acc = 0.0f;
   float G[12];  // sum_k 2 (S_a - S_b) (dS/dl) c_k^T for views a (0..5), b (6..11)
 #pragma unroll
   for (int i = 0; i < 12; ++i) G[i] = 0.0f;
-  if (nk > 0) {
+  if (nk_in > 0) {
     const T* __restrict__ sino = static_cast<const T*>(g.sino);
     const size_t vstride = (size_t)n_alpha * n_s;
     const T* __restrict__ sa = sino + (size_t)pr.a * vstride;
@@ -941,9 +945,16 @@ __device__ __forceinline__ double pair_warp_adjoint(const PairArgs& g, long long
 #pragma unroll
   for (int i = 0; i < 12; ++i)
     for (int o = 16; o > 0; o >>= 1) G[i] += __shfl_xor_sync(0xffffffffu, G[i], o);
+  // a non-finite sum or gradient (non-finite sinogram values) drops the pair:
+  // N_kappa = 0, d = e = 0 and no gradient
+  bool finite = isfinite(acc);
+#pragma unroll
+  for (int i = 0; i < 12; ++i) finite = finite && isfinite(G[i]);
+  const int nk = finite ? nk_in : 0;
   const float d = nk > 0 ? acc / (float)nk : 0.0f;
   const float e = g.cauchy_c > 0.0f ? d / (1.0f + d / g.cauchy_c) : d;
   if (lane == 0) {
+    if (!finite && g.status) atomicOr(g.status, kStatusNonfinitePair);
     if (g.per_pair) {
       g.per_pair[2 * p] = (double)d;
       g.per_pair[2 * p + 1] = (double)e;
@@ -954,7 +965,7 @@ __device__ __forceinline__ double pair_warp_adjoint(const PairArgs& g, long long
     const float scale = nk > 0 ? r * r / (float)nk : 0.0f;
     if (g.Gpp) {  // NULL: a forward evaluation through this code (small n_kappa)
 #pragma unroll
-      for (int i = 0; i < 12; ++i) g.Gpp[12 * p + i] = (double)(G[i] * scale);
+      for (int i = 0; i < 12; ++i) g.Gpp[12 * p + i] = nk > 0 ? (double)(G[i] * scale) : 0.0;
     }
   }
   return (double)e;
@@ -1065,7 +1076,7 @@ __global__ void __launch_bounds__(1024) serve_reduce_kernel(const ServeJob* __re
 cudaError_t launch_ecc_pairs(long long n_pairs, const PairRec* prs, const float4* ctile, int n_tiles,
                              const float4* alpha_dir, const void* sino, const float* scales, int dtype,
                              int n_alpha, int n_s, int K, int W, int H, double cauchy_c, double* per_pair,
-                             int32_t* nk_out, double* block_partial, double* Gpp, int* n_blocks_out,
+                             int32_t* nk_out, double* block_partial, double* Gpp, int* status, int* n_blocks_out,
                              const LaunchHooks& hooks, cudaStream_t stream) {
   // The forward kernel takes two pairs per warp when that still leaves several waves of
   // blocks (the anchor pass then serves both); smaller launches keep one per warp.
@@ -1097,6 +1108,7 @@ cudaError_t launch_ecc_pairs(long long n_pairs, const PairRec* prs, const float4
   g.nk_out = nk_out;
   g.block_partial = block_partial;
   g.Gpp = Gpp;
+  g.status = status;
 #define ECC_LAUNCH(TT)                                                      \
   do {                                                                      \
     if (tiles32)                                                            \

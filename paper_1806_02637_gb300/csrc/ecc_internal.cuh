@@ -58,6 +58,7 @@ struct PairRec {
 enum : int {
   kStatusDegenerateView = 1,
   kStatusDegeneratePair = 2,
+  kStatusNonfinitePair = 4,  // a pair's sum (or its gradient) was not finite: zeroed
 };
 
 // A unit direction (x, y) split into double-float pairs: (hi.x, hi.y, lo.x, lo.y).

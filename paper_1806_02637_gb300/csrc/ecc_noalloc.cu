@@ -12,14 +12,17 @@
 // every call on a device: calls that overlap on the GPU (two streams, two host
 // threads) race on it, so the caller serialises them, e.g. by using one stream.
 //
-// Set-up: the first call on a device resolves the array's device address with
-// cudaGetSymbolAddress (with that device current) and caches it; later calls reuse
-// it.  Make that first call outside any stream capture.
+// Set-up: every call looks up the array's device address with cudaGetSymbolAddress,
+// with the caller's device current (a host-side lookup that allocates nothing).  The
+// address is not cached: after cudaDeviceReset, or after another library in the
+// process resets the primary context, the module is loaded again and the array may
+// sit at a new address, and a cached one would then send the kernels to stale
+// memory.  The first call on a device may load the library's module (lazy module
+// loading), so make it outside any stream capture.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdio>
-#include <mutex>
 
 #include "../../include/ecc.h"
 #include "ecc_internal.cuh"
@@ -50,11 +53,6 @@ constexpr size_t kOffPerPair = align256(kOffPartial + sizeof(double) * ((kMaxPai
 constexpr size_t kOffTiles = align256(kOffPerPair + sizeof(double) * 2 * kMaxPairs);
 constexpr size_t kEnd = kOffTiles + sizeof(float4) * kMaxPairTiles;
 static_assert(kEnd <= kScratchBytes, "no-alloc scratch layout exceeds the static array");
-
-// Device address of the array, resolved once per device with that device current.
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-unsigned char* g_addr[kMaxDevices] = {};
 
 }  // namespace
 
@@ -98,21 +96,18 @@ extern "C" int ecc_evaluate_noalloc(int n_views, const double* P, const double* 
 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return fail(ECC_ECUDA, "no usable current CUDA device");
+  if (e != cudaSuccess) return fail(ECC_ECUDA, "no usable current CUDA device");
+  // the array's address in the current device's context, looked up on every call
   unsigned char* base = nullptr;
   {
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_addr[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess || !p) {
-        cudaGetLastError();
-        std::snprintf(msg, sizeof msg, "cudaGetSymbolAddress of the no-alloc scratch: %s", cudaGetErrorString(e));
-        return fail(ECC_ECUDA, msg);
-      }
-      g_addr[dev] = static_cast<unsigned char*>(p);
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      std::snprintf(msg, sizeof msg, "cudaGetSymbolAddress of the no-alloc scratch: %s", cudaGetErrorString(e));
+      return fail(ECC_ECUDA, msg);
     }
-    base = g_addr[dev];
+    base = static_cast<unsigned char*>(p);
   }
   cudaStream_t s = (cudaStream_t)stream;
   int* status = reinterpret_cast<int*>(base + kOffStatus);
@@ -138,7 +133,7 @@ extern "C" int ecc_evaluate_noalloc(int n_views, const double* P, const double* 
   if ((e = cudaGetLastError()) != cudaSuccess) return fail(ECC_ECUDA, cudaGetErrorString(e));
   int nb = 0;
   e = ecc::launch_ecc_pairs(n_pairs, prs, ctile, n_tiles, adir, sino, scales, dtype, n_alpha, n_s, n_kappa, W, H,
-                            cauchy_c, per_pair, nkappa, partial, nullptr, &nb, hk, s);
+                            cauchy_c, per_pair, nkappa, partial, nullptr, status, &nb, hk, s);
   if (e != cudaSuccess) return fail(ECC_ECUDA, cudaGetErrorString(e));
   e = ecc::launch_reduce(partial, nb, total, hk, s);
   if (e != cudaSuccess) return fail(ECC_ECUDA, cudaGetErrorString(e));

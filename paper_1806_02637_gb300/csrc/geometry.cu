@@ -63,6 +63,7 @@ __host__ __device__ bool view_geometry(const T* Pm, int W, int H, T* Pn, T* C, T
   const T det = dot3(m1, c23);
   const T n3 = sqrt(dot3(m3, m3));
   bool ok = isfinite(value(det)) && isfinite(value(n3)) && value(det) != 0.0 && value(n3) > 0.0;
+  for (int k = 0; k < 12; ++k) ok = ok && isfinite(value(Pm[k]));  // NaN / Inf anywhere, the motion's included
   const T sc = ok ? T(copysign(1.0, value(det))) / n3 : T(0.0);
   for (int k = 0; k < 12; ++k) Pn[k] = Pm[k] * sc;
   const T* a = Pn;
@@ -237,14 +238,16 @@ __device__ ViewTan view_tangent(const double* P, const double* motion, int W, in
   }
   D6 Pm[12], Pn[12], C[3], up[3], cofc[9], u0, v0, D;
   moved_projection(P, th, Pm);
-  view_geometry(Pm, W, H, Pn, C, up, cofc, &u0, &v0, &D);
+  // a degenerate view's pairs carry no gradient; zero tangents keep its row at 0
+  // (its NaN / Inf geometry would otherwise turn 0 x tangent into NaN)
+  const double ok = view_geometry(Pm, W, H, Pn, C, up, cofc, &u0, &v0, &D) ? 1.0 : 0.0;
   ViewTan t;
   for (int j = 0; j < 6; ++j) {
     for (int k = 0; k < 3; ++k) {
-      t.dC[k][j] = C[k].d[j];
-      t.dup[k][j] = up[k].d[j];
+      t.dC[k][j] = ok ? C[k].d[j] : 0.0;
+      t.dup[k][j] = ok ? up[k].d[j] : 0.0;
     }
-    for (int k = 0; k < 9; ++k) t.dcofc[k][j] = cofc[k].d[j];
+    for (int k = 0; k < 9; ++k) t.dcofc[k][j] = ok ? cofc[k].d[j] : 0.0;
   }
   return t;
 }
@@ -275,13 +278,13 @@ __global__ void view_tangent_P_kernel(int n_views, const double* __restrict__ P,
   } else {
     for (int k = 0; k < 12; ++k) Pm[k] = Pd[k];
   }
-  view_geometry(Pm, W, H, Pn, C, up, cofc, &u0, &v0, &D);
+  const bool ok = view_geometry(Pm, W, H, Pn, C, up, cofc, &u0, &v0, &D);  // degenerate: zero tangents
   ViewTanP& t = out[lam];
   for (int k = 0; k < 3; ++k) {
-    t.d[k][j] = C[k].d[0];
-    t.d[3 + k][j] = up[k].d[0];
+    t.d[k][j] = ok ? C[k].d[0] : 0.0;
+    t.d[3 + k][j] = ok ? up[k].d[0] : 0.0;
   }
-  for (int k = 0; k < 9; ++k) t.d[6 + k][j] = cofc[k].d[0];
+  for (int k = 0; k < 9; ++k) t.d[6 + k][j] = ok ? cofc[k].d[0] : 0.0;
 }
 
 namespace {

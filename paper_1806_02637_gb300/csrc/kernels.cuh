@@ -70,6 +70,7 @@ struct PairArgs {
   int32_t* nk_out;
   double* block_partial;
   double* Gpp;  // adjoint output, NULL for the plain evaluation
+  int* status;  // device status word (kStatus* bits OR-ed in), or NULL
 };
 
 inline void pair_args_grid(PairArgs& g, int n_alpha, int n_s, int W, int H) {
@@ -99,8 +100,8 @@ size_t radon_plane_bytes(int W, int H, int n_s);
 cudaError_t launch_ecc_pairs(long long n_pairs, const PairRec* prs, const float4* ctile, int n_tiles,
                              const float4* alpha_dir, const void* sino, const float* scales, int dtype,
                              int n_alpha, int n_s, int K, int W, int H, double cauchy_c, double* per_pair, int32_t* nk_out,
-                             double* block_partial, double* Gpp, int* n_blocks_out, const LaunchHooks& hooks,
-                             cudaStream_t stream);
+                             double* block_partial, double* Gpp, int* status, int* n_blocks_out,
+                             const LaunchHooks& hooks, cudaStream_t stream);
 
 cudaError_t launch_reduce(const double* partial, int n, double* total, const LaunchHooks& hooks,
                           cudaStream_t stream);

@@ -294,6 +294,8 @@ void finish_job(ecc_serve* S, Job* J) {
     std::memcpy(d.nodes_out, theta + 6 * d.n_views, sizeof(double) * 6 * d.n_nodes);
   J->t_done = Clock::now();
   ecc_result& r = J->res;
+  const size_t nn = d.motion_model == ECC_MOTION_AKIMA ? (size_t)d.n_nodes : 0;
+  std::memcpy(&r.flags, J->h_stage + (d.n_iters + 1) + 6 * d.n_views + 6 * nn, sizeof(int));
   r.iters = d.n_iters;
   r.total_first = totals[0];
   r.total_last = totals[d.n_iters];
@@ -385,6 +387,7 @@ void round_loop(ecc_serve* S) {
       s.pair.nk_out = nullptr;
       s.pair.block_partial = (double*)(R + L.partial);
       s.pair.Gpp = (double*)(R + L.Gpp);
+      s.pair.status = (int*)(R + L.status);
       s.dtype = d.dtype;
       s.n_views = d.n_views;
       s.W = d.W;
@@ -440,9 +443,13 @@ void round_loop(ecc_serve* S) {
                         s);
         cudaMemcpyAsync(J->h_stage + (d.n_iters + 1), J->dev + J->L.theta, sizeof(double) * 6 * d.n_views,
                         cudaMemcpyDeviceToHost, s);
-        if (d.motion_model == ECC_MOTION_AKIMA)
+        const size_t nn = d.motion_model == ECC_MOTION_AKIMA ? (size_t)d.n_nodes : 0;
+        if (nn)
           cudaMemcpyAsync(J->h_stage + (d.n_iters + 1) + 6 * d.n_views, J->dev + J->L.nodes,
-                          sizeof(double) * 6 * d.n_nodes, cudaMemcpyDeviceToHost, s);
+                          sizeof(double) * 6 * nn, cudaMemcpyDeviceToHost, s);
+        // the job's device status word (ECC_STATUS_* bits), in the next double's slot
+        cudaMemcpyAsync(J->h_stage + (d.n_iters + 1) + 6 * d.n_views + 6 * nn, J->dev + J->L.status, sizeof(int),
+                        cudaMemcpyDeviceToHost, s);
         if (!J->done) cudaEventCreateWithFlags(&J->done, cudaEventDisableTiming);
         cudaEventRecord(J->done, s);
         J->st = State::Finishing;
@@ -478,8 +485,18 @@ int check_job(const ecc_job* j, std::string* why) {
     return bad("n_nodes out of range [3, n_views] for the Akima motion model");
   if (j->param_mask < 0 || j->param_mask > 0x3F) return bad("param_mask has bits beyond the six parameters");
   const size_t nn = j->motion_model == ECC_MOTION_AKIMA ? (size_t)j->n_nodes : 0;
-  if (sizeof(double) * ((size_t)j->n_iters + 1 + 6 * (size_t)j->n_views + 6 * nn) > kSlotBytes)
+  if (sizeof(double) * ((size_t)j->n_iters + 2 + 6 * (size_t)j->n_views + 6 * nn) > kSlotBytes)
     return bad("n_iters + 6 n_views + 6 n_nodes too large for the result staging");
+  // the geometry is small enough to check on the host; the images are checked on the
+  // device (a non-finite sinogram value drops the pairs it reaches, see ecc_result.flags)
+  auto all_finite = [](const double* x, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+      if (!std::isfinite(x[i])) return false;
+    return true;
+  };
+  if (!all_finite(j->P, 12 * (size_t)j->n_views)) return bad("P has a non-finite entry");
+  if (j->motion0 && !all_finite(j->motion0, 6 * (size_t)j->n_views)) return bad("motion0 has a non-finite entry");
+  if (nn && j->nodes0 && !all_finite(j->nodes0, 6 * nn)) return bad("nodes0 has a non-finite entry");
   return ECC_OK;
 }
 

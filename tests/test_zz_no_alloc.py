@@ -33,6 +33,10 @@ def _case(name):
         cfg, views, K, c, dtype = synth.CONFIGS["c2"], tuple(range(0, 496, 21)), 512, 0.0, torch.float32
     elif name == "c3-motion-pairs":
         cfg, views, K, c, dtype = synth.CONFIGS["c3"], tuple(range(0, 248, 15)), 256, 5.0, torch.float32
+    elif name == "c4-k77-bf16":
+        # n_kappa below 96: the 32-sample-tile forward kernel with a ragged last tile
+        # (77 = 2 x 32 + 13), BF16 storage, opposed views (full-pi arcs)
+        cfg, views, K, c, dtype = synth.CONFIGS["c4"], (0, 7, 310, 620, 627), 77, 0.0, torch.bfloat16
     else:  # "c1-f16"
         cfg, views, K, c, dtype = synth.CONFIGS["c1"], None, 256, 0.0, torch.float16
     sc = H.scan(cfg.name, views)
@@ -81,13 +85,13 @@ def _check(case, out):
 
 
 def test_noalloc_matches_ecc_evaluate_on_calls_in_a_row():
-    names = ["c2-all", "c3-motion-pairs", "c1-f16"]
+    names = ["c2-all", "c3-motion-pairs", "c1-f16", "c4-k77-bf16"]
     cases = [_case(n) for n in names]
     outs = [_outputs(c) for c in cases]
     reps = [_outputs(c) for c in cases[:2]]
     torch.cuda.synchronize()
-    # first call on the device (resolves the scratch address), then calls in a row
-    # on one stream with no host synchronisation between them
+    # calls in a row on one stream with no host synchronisation between them (each
+    # looks up the scratch address; the first may load the library's module)
     for case, out in zip(cases, outs):
         _noalloc(case, out)
     torch.cuda.synchronize()
