@@ -1,8 +1,8 @@
 """One small, repeatable launch sequence per kernel family, for profilers.
 
-    python -m paper_1806_02637_gb300.profile_case --case radon  [--views 32]
-    python -m paper_1806_02637_gb300.profile_case --case pairs  [--views 128]
-    python -m paper_1806_02637_gb300.profile_case --case grad   [--views 128]
+    python profile_case.py --case radon  [--views 32]
+    python profile_case.py --case pairs  [--views 128]
+    python profile_case.py --case grad   [--views 128]
 
 Each case builds a seeded subset of the 496-view short scan (620 x 480 detector,
 768 x 768 dRadon/ds grid, 512 kappa), runs the call three times untimed and three
@@ -13,9 +13,14 @@ capture a warm one.  The inputs stay well below a few GB of device memory.
 from __future__ import annotations
 
 import argparse
+import os
 import sys
 
 import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
 
 
 def main(argv=None) -> int:
