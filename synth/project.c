@@ -47,6 +47,13 @@ static double ray_integral(const double src[3], const double dir[3], const doubl
             double dist2 = px * px + py * py + pz * pz;
             total += q[1] * sqrt(2.0 * M_PI) * sig * exp(-dist2 / (2.0 * sig * sig));
         } else {
+            /* a ray that misses the bounding sphere (radius: the largest semi-axis)
+               misses the ellipsoid: skip the exact chord (same result, cheaper) */
+            double rad = q[5] > q[6] ? q[5] : q[6];
+            rad = rad > q[7] ? rad : q[7];
+            double t = -(d[0] * dir[0] + d[1] * dir[1] + d[2] * dir[2]);
+            double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (dd - t * t > rad * rad * (1.0 + 1e-9)) continue;
             const double* R = q + 8;
             double p[3], r[3];
             for (int i = 0; i < 3; ++i) {
