@@ -39,7 +39,9 @@ METRIC = "ECC line-pair samples/s"
 UNIT = "line-pair samples/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 L1_PEAK_TBS = 128.0 * 152 * 2.07e9 / 1e12  # L1 data bytes per second (unit counts x max SM clock)
-FLOPS_PER_TAP = 4                                    # lerp (sub + fma) + accumulate
+# FP32 work of one Joseph tap written directly: position x0 + k dx (an FMA, 2 FLOP), floor
+# and fraction (2), the lerp v0 + f (v1 - v0) (a subtraction and an FMA, 3), accumulate (1)
+FLOPS_PER_TAP = 8
 
 
 def parse_args(argv=None):
@@ -56,6 +58,13 @@ def parse_args(argv=None):
                     help="skip the gradient legs (motion gradient and calibration gradient on the same sinograms)")
     ap.add_argument("--no-storage-forms", action="store_true",
                     help="skip the FP16/BF16 sinogram storage leg (evaluation against the FP32 form)")
+    ap.add_argument("--no-c4", dest="c4_leg", action="store_false",
+                    help="skip the precision leg (1240-view 976x976 scan, FP16/BF16 sinograms, 1024 kappa)")
+    ap.add_argument("--shard", action="store_true",
+                    help="N > 1: one job over all ranks (view slices + all-gather of the sinograms, pair tiles + "
+                         "FP64 all-reduce; strong scaling) instead of one independent job per rank (weak scaling)")
+    ap.add_argument("--ref-stride", type=int, default=3,
+                    help="reference arm: the pairs timed per step are those among every ref-stride-th view")
     ap.add_argument("--serve-jobs", type=int, default=24, help="jobs of the serving leg")
     ap.add_argument("--serve-rate", type=float, default=20.0, help="mean Poisson arrival rate [jobs/s]")
     ap.add_argument("--views", type=int, default=0,
@@ -256,6 +265,7 @@ def serving_leg(args, c2_scan):
         time.sleep(0.0005)
     wall = max(r["t_done"] for r in results.values()) - t_arr[0]
     st = ecc.ecc_serve_stats(ctx)
+    dev_t = ecc.ecc_serve_times(ctx)
     lat = np.array([results[j]["latency_ms"] for j in sorted(results)])
     que = np.array([results[j]["queue_ms"] for j in sorted(results)])
     lp = sum(r["line_pairs"] for r in results.values())
@@ -271,6 +281,23 @@ def serving_leg(args, c2_scan):
         ref = float(ecc.ecc_evaluate(ctx, Pd, S, W, H, K, motion=torch.from_numpy(th).cuda(),
                                      want_per_pair=False)["total"].cpu()[0])
         acc.append(abs(results[j]["total_first"] - ref) / abs(ref))
+    # the same jobs, one after the other, through plain calls on one stream: upload,
+    # precompute, n_iters x (ecc_evaluate_grad, step), final ecc_evaluate
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _, det, P, I, K, th in jobs:
+        W, H, _, na, ns, _ = SERVE_DETECTORS[det]
+        Pd, Id = P.cuda(non_blocking=True), I.cuda(non_blocking=True)
+        S, scales = ecc.ecc_precompute_radon_derivative(ctx, Pd, Id, na, ns, dtype=torch.float16)
+        del Id
+        theta = torch.from_numpy(th).cuda()
+        for _ in range(iters):
+            g = ecc.ecc_evaluate_grad(ctx, Pd, S, W, H, K, motion=theta, scales=scales, want_per_pair=False)["grad"]
+            theta -= step * g
+        ecc.ecc_evaluate(ctx, Pd, S, W, H, K, motion=theta, scales=scales, want_per_pair=False)
+        del S, scales
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
     ctx.close()
     return {"metric": "ECC line-pair samples/s, served (FP16 storage, with gradients)", "value": lp / wall,
             "unit": UNIT, "jobs": len(results), "wall_s": wall, "arrival_rate_per_s": args.serve_rate,
@@ -278,6 +305,14 @@ def serving_leg(args, c2_scan):
                            "max": float(lat.max())},
             "queue_ms": {"p50": float(np.percentile(que, 50)), "p99": float(np.percentile(que, 99))},
             "rounds": st["rounds"], "mean_jobs_per_round": st["job_rounds"] / max(1, st["rounds"]),
+            "device_time_ms": dev_t,
+            "shares_of_wall": {"upload": dev_t["upload_ms"] / 1e3 / wall, "precompute": dev_t["precompute_ms"] / 1e3 / wall,
+                               "rounds": dev_t["round_ms"] / 1e3 / wall,
+                               "note": "device time of each part over the wall time; admissions overlap rounds, so "
+                                       "the parts may sum above 1"},
+            "plain_calls_same_jobs": {"value": lp / plain_s, "unit": UNIT, "wall_s": plain_s,
+                                      "how": "the same jobs back to back, no arrival process: upload, precompute, "
+                                             f"{iters} x (ecc_evaluate_grad + step), ecc_evaluate, one stream"},
             "max_jobs_per_round": st["max_batch"], "iterations_per_job": iters, "step": step,
             "fp16_vs_fp32_total_rel_err": {"jobs": len(acc), "max": float(max(acc)) if acc else None},
             "jobs_mix": "detector uniform {256^2, 620x480, 976^2}, views U{50..500}, kappa U{256..1024}, "
@@ -287,52 +322,92 @@ def serving_leg(args, c2_scan):
 
 
 # ------------------------------------------------------------------ CPU baseline
-def sample_views(cfg, n_views_sample: int):
-    return np.linspace(0, cfg.n_views - 1, n_views_sample).round().astype(int)
+def oracle_energies(orc, P, S, W, H, K, pairs):
+    """E_ab of each pair (reading R10): the mean of (S_a^2 + S_b^2) / 2 over the pair's
+    valid planes, from the oracle with zero-sinogram copies of the views."""
+    n = S.shape[0]
+    P2 = np.concatenate([P, P])
+    S2 = np.concatenate([S, np.zeros_like(S)])
+    pairs = np.asarray(pairs)
+    ea = orc.ecc(P2, S2, W, H, K, pairs=np.stack([pairs[:, 0], pairs[:, 1] + n], axis=1))["d"]
+    eb = orc.ecc(P2, S2, W, H, K, pairs=np.stack([pairs[:, 0] + n, pairs[:, 1]], axis=1))["d"]
+    return 0.5 * (ea + eb)
 
 
-def oracle_sample(cfg, scan, n_views_sample: int, n_threads: int, sampled: bool = False):
-    """Times the oracle on a bounded sample of the workload: the dRadon/ds of
-    n_views_sample views and the ECC of all pairs among them; extrapolates the
-    per-view and per-pair costs to the whole job.  `scan` holds either all views
-    or (sampled=True) only the views of sample_views()."""
+def error_stats(d, d_ref, E, total, total_ref):
+    """Errors of one result against the FP64 oracle: per pair plain |dd| / d and with
+    reading R10's floor |dd| / max(d, 1e-2 E); the total plain."""
+    d, d_ref = np.asarray(d, dtype=np.float64), np.asarray(d_ref, dtype=np.float64)
+    plain = np.abs(d - d_ref) / np.maximum(d_ref, 1e-300)
+    floored = np.abs(d - d_ref) / np.maximum(d_ref, 1e-2 * np.asarray(E))
+    q = lambda x: {"max": float(x.max()), "p99": float(np.percentile(x, 99)), "median": float(np.median(x))}
+    return {"pairs": int(d.size), "pair_plain": q(plain), "pair_floored": q(floored),
+            "total_rel_err": float((total - total_ref) / total_ref)}
+
+
+def oracle_job(cfg, scan, n_threads: int):
+    """The oracle on the whole job: dRadon/ds of every view and the ECC of every pair,
+    each timed (FP64, n_threads host threads)."""
     from oracle import oracle as orc
-    idx = slice(None) if sampled else sample_views(cfg, n_views_sample)
-    P = scan["P"][idx]
-    imgs = scan["images"][idx]
     t0 = time.perf_counter()
-    S = orc.radon_derivative(P, imgs, cfg.n_alpha, cfg.n_s, n_threads=n_threads)
+    S = orc.radon_derivative(scan["P"], scan["images"], cfg.n_alpha, cfg.n_s, n_threads=n_threads)
     t1 = time.perf_counter()
-    r = orc.ecc(P, S, cfg.W, cfg.H, cfg.K, n_threads=n_threads)
+    r = orc.ecc(scan["P"], S, cfg.W, cfg.H, cfg.K, n_threads=n_threads)
     t2 = time.perf_counter()
-    n_pairs_sample = len(r["d"])
-    t_job = (t1 - t0) / n_views_sample * cfg.n_views + (t2 - t1) / n_pairs_sample * cfg.n_pairs
-    value = cfg.n_pairs * cfg.K / t_job
-    return value, {"radon_s": t1 - t0, "ecc_s": t2 - t1, "views": n_views_sample, "pairs": n_pairs_sample,
-                   "job_s_extrapolated": t_job}
+    return S, r, t1 - t0, t2 - t1
+
+
+def reference_sample(cfg, stride=3):
+    """The views and pairs one step of the reference arm times: the dRadon/ds of 8 views
+    (a different 8 each step, over the whole scan) and the ECC of all pairs among every
+    stride-th view (stride 3: 166 views, 13,695 pairs), whose sinograms the oracle
+    computes once before the steps."""
+    pv = np.arange(0, cfg.n_views, stride)
+    return pv, synth.upper_pairs(len(pv))
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands, on the host cores, on the same
+    workload.  A step times a bounded sample (reference_sample) and the rate is
+    extrapolated per view and per pair to the whole job; ms_per_step is the measured
+    time of one step's sample, so steps x ms_per_step is the time actually measured."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    from oracle import oracle as orc
     cfg = synth.CONFIGS[args.workload]
-    scan = synth.make_scan(cfg, views=sample_views(cfg, 12))
+    scan = synth.make_scan(cfg)
     cores = os.cpu_count() or 1
-    vals, infos = [], []
+    pv, pairs = reference_sample(cfg, args.ref_stride)
+    S_pv = orc.radon_derivative(scan["P"][pv], scan["images"][pv], cfg.n_alpha, cfg.n_s, n_threads=cores)
+    nv_step = 8
+    t_radon = t_ecc = 0.0
+    sample_s = []
     for it in range(args.warmup + args.steps):
-        v, info = oracle_sample(cfg, scan, 12, cores, sampled=True)
+        views = (it * nv_step + np.arange(nv_step) * (cfg.n_views // nv_step)) % cfg.n_views
+        t0 = time.perf_counter()
+        orc.radon_derivative(scan["P"][views], scan["images"][views], cfg.n_alpha, cfg.n_s, n_threads=cores)
+        t1 = time.perf_counter()
+        orc.ecc(scan["P"][pv], S_pv, cfg.W, cfg.H, cfg.K, pairs=pairs, n_threads=cores)
+        t2 = time.perf_counter()
         if it >= args.warmup:
-            vals.append(v)
-            infos.append(info)
-    value = statistics.median(vals)
-    ms = cfg.n_pairs * cfg.K / value * 1e3
-    sample = (f"per step: dRadon/ds of 12 of the {cfg.n_views} views and the ECC of the 66 pairs among them, "
-              f"extrapolated per view and per pair to the whole job")
+            t_radon += t1 - t0
+            t_ecc += t2 - t1
+            sample_s.append(t2 - t0)
+    per_view = t_radon / (args.steps * nv_step)
+    per_pair = t_ecc / (args.steps * len(pairs))
+    job_s = per_view * cfg.n_views + per_pair * cfg.n_pairs
+    value = cfg.n_pairs * cfg.K / job_s
+    sample = (f"per step: dRadon/ds of {nv_step} of the {cfg.n_views} views (a different {nv_step} each step) and the "
+              f"ECC of the {len(pairs)} pairs among every {args.ref_stride}th view, on {cores} host threads; measured "
+              f"{per_view:.3f} s per view and {per_pair * 1e3:.4f} ms per pair over {args.steps} steps "
+              f"({t_radon:.2f} s + {t_ecc:.2f} s), extrapolated to the whole job ({job_s:.1f} s)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(sample_s),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "extrapolated": True,
+            "sample_per_step": {"views_radon": nv_step, "pairs_ecc": int(len(pairs)), "n_kappa": cfg.K},
             "config": workload_config(cfg),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -341,12 +416,14 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ storage forms
-def storage_forms(ctx, P, images, cfg, total_f32, reps=10):
+def storage_forms(ctx, P, images, cfg, total_f32, reps=10, oracle=None, l2_gbs=None):
     """The reduced-precision form: the same scan's sinograms stored in FP16 (per-view
     scale) and BF16, then the evaluation of all pairs timed as in the FP32 form (the
     library's CUDA events, inputs resident).  Reports line-pair samples/s of the
-    evaluation, the pair kernel against HBM at 16 B per line pair, and the total's
-    relative difference from the plain FP32 form on the same GPU."""
+    evaluation, the pair kernel against HBM and L2 at 16 B per line pair, the total's
+    relative difference from the plain FP32 form on the same GPU, and (with the
+    oracle's result of the job) every pair's and the total's error against the FP64
+    oracle."""
     import torch
     import paper_1806_02637_gb300 as ecc
     units = cfg.n_pairs * cfg.K
@@ -372,10 +449,122 @@ def storage_forms(ctx, P, images, cfg, total_f32, reps=10):
         t = float(tot.cpu()[0])
         out[name] = {"ms_per_eval": eval_ms, "line_pairs_per_s": units / (eval_ms / 1e3), "pair_kernel_ms": pk_ms,
                      "pair_kernel_gather_gbs": gbs, "pair_kernel_frac_of_hbm": gbs / peaks.get("hbm_gbs", 6800.0),
+                     "pair_kernel_frac_of_l2": gbs / l2_gbs if l2_gbs else None,
                      "total": t, "total_rel_diff_vs_f32": abs(t - total_f32) / abs(total_f32)}
+        if oracle is not None:
+            r = ecc.ecc_evaluate(ctx, P, S, cfg.W, cfg.H, cfg.K, scales=scales)
+            out[name]["vs_oracle"] = error_stats(r["per_pair"][:, 0].cpu().numpy(), oracle["d"], oracle["E"],
+                                                 float(r["total"].cpu()[0]), oracle["total"])
         del S, scales
     out["note"] = ("evaluation only (view/pair set-up, pair kernel, reduction), 16 B per line pair for the gather; "
-                   "the sinograms come from the same precompute in the stated storage type")
+                   "the sinograms come from the same precompute in the stated storage type; vs_oracle: every pair "
+                   "against the FP64 oracle's result of the job (pair_floored uses reading R10's 1e-2 E_ab floor)")
+    return out
+
+
+def l2_read_rate(dev, mb=48, reps=200):
+    """Read rate of a buffer resident in L2 (48 MB of the 129 MB): torch.sum over it,
+    timed with CUDA events; the denominator of the L2 fractions."""
+    import torch
+    x = torch.ones((mb * (1 << 20)) // 4, dtype=torch.float32, device=dev)
+    for _ in range(10):
+        x.sum()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(reps):
+        x.sum()
+    ev1.record()
+    torch.cuda.synchronize(dev)
+    gbs = reps * x.numel() * 4 / (ev0.elapsed_time(ev1) / 1e3) / 1e9
+    del x
+    return {"gbs": gbs, "how": f"torch.sum over a resident {mb} MB FP32 buffer, {reps} times, CUDA events"}
+
+
+# ------------------------------------------------------------------ precision leg (1240-view scan)
+def c4_leg(ctx, l2_gbs, reps=5):
+    """The precision workload: 1240 views over 360 degrees, 976x976 detector (0.3 mm),
+    60 seeded ellipsoids, 1024 x 1382 dRadon/ds stored in FP16 and BF16, 1024 kappa, all
+    768,180 pairs.  Times the precompute and the evaluation (the library's CUDA events,
+    inputs resident), the pair kernel's algorithmic bytes (16 B per line pair) against
+    HBM and L2, and the oracle on 16 seeded views: their dRadon/ds and the 120 pairs
+    among them (timed, and extrapolated per view and per pair to the whole job), with
+    those pairs' errors against the oracle and the stored sinograms' errors."""
+    import torch
+    import paper_1806_02637_gb300 as ecc
+    from oracle import oracle as orc
+    cfg = synth.CONFIGS["c4"]
+    peaks = measured_peaks()
+    t0 = time.perf_counter()
+    scan = synth.make_scan(cfg)
+    gen_s = time.perf_counter() - t0
+    dev = torch.device("cuda", torch.cuda.current_device())
+    P = torch.from_numpy(scan["P"]).to(dev)
+    images = torch.from_numpy(scan["images"]).to(dev)
+    units = cfg.n_pairs * cfg.K
+    views = np.sort(np.random.default_rng(1240).choice(cfg.n_views, 16, replace=False))
+    sub = synth.upper_pairs(16)
+    ga, gb = views[sub[:, 0]], views[sub[:, 1]]
+    flat = ga * (2 * cfg.n_views - ga - 1) // 2 + (gb - ga - 1)
+    cores = os.cpu_count() or 1
+    ta = time.perf_counter()
+    S_or = orc.radon_derivative(scan["P"][views], scan["images"][views], cfg.n_alpha, cfg.n_s, n_threads=cores)
+    tb = time.perf_counter()
+    r_or = orc.ecc(scan["P"][views], S_or, cfg.W, cfg.H, cfg.K, pairs=sub, n_threads=cores)
+    tc = time.perf_counter()
+    E_or = oracle_energies(orc, scan["P"][views], S_or, cfg.W, cfg.H, cfg.K, sub)
+    job_s = (tb - ta) / 16 * cfg.n_views + (tc - tb) / len(sub) * cfg.n_pairs
+    out = {"workload": (f"c4: {cfg.n_views}-view 360-degree scan, {cfg.W}x{cfg.H} detector ({cfg.pixel_mm} mm), "
+                        f"{cfg.n_prim} seeded ellipsoids, {cfg.n_alpha}x{cfg.n_s} dRadon/ds, {cfg.K} kappa, all "
+                        f"{cfg.n_pairs} pairs"),
+           "line_pairs": units, "scan_generation_s": gen_s,
+           "cpu_baseline": {"value": units / job_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "extrapolated": True,
+                            "sample": (f"dRadon/ds of 16 seeded views ({tb - ta:.2f} s) and the ECC of the 120 pairs "
+                                       f"among them ({tc - tb:.3f} s), extrapolated per view and per pair to the "
+                                       f"whole job ({job_s:.0f} s)")}}
+    for name, dt in (("float16", torch.float16), ("bfloat16", torch.bfloat16)):
+        S, scales = ecc.ecc_precompute_radon_derivative(ctx, P, images, cfg.n_alpha, cfg.n_s, dtype=dt)
+        torch.cuda.synchronize()
+        ecc.ecc_profile_read(ctx)
+        ecc.ecc_profile_enable(ctx, True)
+        ecc.ecc_precompute_radon_derivative(ctx, P, images, cfg.n_alpha, cfg.n_s, dtype=dt, out=S, scales=scales)
+        torch.cuda.synchronize()
+        pre = ecc.ecc_profile_read(ctx)
+        tot = torch.empty((1,), dtype=torch.float64, device=dev)
+        for _ in range(2):
+            ecc.ecc_evaluate(ctx, P, S, cfg.W, cfg.H, cfg.K, scales=scales, total=tot, want_per_pair=False)
+        torch.cuda.synchronize()
+        ecc.ecc_profile_read(ctx)
+        for _ in range(reps):
+            ecc.ecc_evaluate(ctx, P, S, cfg.W, cfg.H, cfg.K, scales=scales, total=tot, want_per_pair=False)
+        torch.cuda.synchronize()
+        prof = ecc.ecc_profile_read(ctx)
+        ecc.ecc_profile_enable(ctx, False)
+        eval_ms = sum(prof[n][1] for n in ("alpha_dir_kernel", "pair_setup_kernel", "ecc_pair_kernel",
+                                           "reduce_kernel") if n in prof) / reps
+        pk_ms = prof["ecc_pair_kernel"][1] / prof["ecc_pair_kernel"][0]
+        gbs = 16.0 * units / (pk_ms / 1e3) / 1e9
+        r = ecc.ecc_evaluate(ctx, P, S, cfg.W, cfg.H, cfg.K, scales=scales)
+        d = r["per_pair"][:, 0].cpu().numpy()
+        stored = S[torch.as_tensor(views, device=dev)].float()
+        if scales is not None:
+            stored = stored * scales[torch.as_tensor(views, device=dev)][:, None, None]
+        stored = stored.cpu().numpy().astype(np.float64)
+        sino_err = (np.abs(stored - S_or).reshape(16, -1).max(axis=1) / np.abs(S_or).reshape(16, -1).max(axis=1))
+        out[name] = {"precompute_ms": sum(ms for _, ms in pre.values()), "ms_per_eval": eval_ms,
+                     "line_pairs_per_s": units / (eval_ms / 1e3), "pair_kernel_ms": pk_ms,
+                     "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks.get("hbm_gbs", 6800.0),
+                                  "unit": "GB/s", "frac": gbs / peaks.get("hbm_gbs", 6800.0),
+                                  "frac_of_l2": gbs / l2_gbs, "work": "16 B (2 views x 4 taps x 2 B) per line pair"},
+                     "total": float(r["total"].cpu()[0]),
+                     "vs_oracle_120_pairs": error_stats(d[flat], r_or["d"], E_or, float(d[flat].sum()),
+                                                        float(r_or["d"].sum())),
+                     "stored_sinogram_err_max_over_16_views": float(sino_err.max())}
+        del S, scales, r
+        torch.cuda.empty_cache()
+    del images, P
+    torch.cuda.empty_cache()
     return out
 
 
@@ -437,7 +626,14 @@ def run_ours(args):
     sino = torch.empty((cfg.n_views, cfg.n_alpha, cfg.n_s), dtype=torch.float32, device=dev)
     total = torch.empty((1,), dtype=torch.float64, device=dev)
 
+    shard = args.shard and world > 1
+
     def step():
+        if shard:   # one job over all ranks: view slices, all-gather, pair tiles, FP64 all-reduce
+            from paper_1806_02637_gb300 import distributed as D
+            t, _ = D.sharded_consistency(ctx, P, images, cfg.W, cfg.H, cfg.n_alpha, cfg.n_s, cfg.K, rank, world)
+            total.copy_(t)
+            return
         ecc.ecc_precompute_radon_derivative(ctx, P, images, cfg.n_alpha, cfg.n_s, out=sino)
         ecc.ecc_evaluate(ctx, P, sino, cfg.W, cfg.H, cfg.K, total=total, want_per_pair=False)
 
@@ -474,7 +670,7 @@ def run_ours(args):
     elapsed_ms = max_over_ranks(pg, elapsed_ms, dev)
     ms_per_step = elapsed_ms / args.steps
     units = cfg.n_pairs * cfg.K
-    value = units * world / (ms_per_step / 1e3)
+    value = units * (1 if shard else world) / (ms_per_step / 1e3)
 
     e2e = None
     if not args.no_e2e:
@@ -554,29 +750,50 @@ def run_ours(args):
                      # DRAM read + write and L2 sector bytes per launch
                      "pair_kernel_dram_bytes_ncu": 446589952 + 23083776,
                      "pair_kernel_l2_bytes_ncu": 81681858 * 32}
+    l2 = l2_read_rate(dev)
+    if eval_only:
+        eval_only["pair_kernel_frac_of_l2"] = eval_only["pair_kernel_gather_gbs"] / l2["gbs"]
+        eval_only["l2_read_probe"] = l2
     adjoint = None
     if not args.no_adjoint_forms:
         adjoint = adjoint_forms(ctx, P, sino, cfg)
+    # the oracle on the whole job (FP64, host cores): the CPU baseline, and the reference
+    # every result of this line is compared with
+    cpu = oracle = None
+    if not args.no_cpu_baseline and world == 1:
+        from oracle import oracle as orc
+        cores = os.cpu_count() or 1
+        S_or, r_or, t_radon, t_ecc = oracle_job(cfg, scan, cores)
+        cpu = {"value": units / (t_radon + t_ecc), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": (f"the whole job, not extrapolated: dRadon/ds of all {cfg.n_views} views ({t_radon:.2f} s) "
+                          f"and the ECC of all {cfg.n_pairs} pairs ({t_ecc:.2f} s), FP64 on {cores} host threads")}
+        E_or = oracle_energies(orc, scan["P"], S_or, cfg.W, cfg.H, cfg.K, r_or["pairs"])
+        del S_or
+        oracle = {"d": r_or["d"], "total": r_or["total"], "E": E_or}
+    accuracy = None
+    if oracle is not None:
+        r32 = ecc.ecc_evaluate(ctx, P, sino, cfg.W, cfg.H, cfg.K)
+        accuracy = error_stats(r32["per_pair"][:, 0].cpu().numpy(), oracle["d"], oracle["E"],
+                               float(r32["total"].cpu()[0]), oracle["total"])
+        accuracy["oracle_total"] = oracle["total"]
     forms = None
     if not args.no_storage_forms:
-        forms = storage_forms(ctx, P, images, cfg, result_total)
+        forms = storage_forms(ctx, P, images, cfg, result_total, oracle=oracle, l2_gbs=l2["gbs"])
     serving = None
     if not args.no_serving and world == 1:
         serving = serving_leg(args, scan)
-    cpu = None
-    if not args.no_cpu_baseline and world == 1:
-        cores = os.cpu_count() or 1
-        v, info = oracle_sample(cfg, scan, 48, cores)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": (f"dRadon/ds of {info['views']} of the {cfg.n_views} views ({info['radon_s']:.1f} s) and ECC "
-                          f"of the {info['pairs']} pairs among them ({info['ecc_s']:.1f} s), extrapolated per view "
-                          f"and per pair to the whole job ({info['job_s_extrapolated']:.0f} s)")}
+    precision_c4 = None
+    if args.c4_leg and world == 1:
+        del images, sino
+        torch.cuda.empty_cache()
+        precision_c4 = c4_leg(ctx, l2["gbs"])
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(cfg),
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "strong" if shard else "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": dict(workload_config(cfg), **({"parallelism": f"one job over {world} ranks: view slices + all-gather of the sinograms, pair tiles + FP64 all-reduce"} if shard else {})),
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
-            "kernels": kern, "ecc_eval_only": eval_only, "storage_forms": forms, "adjoint_forms": adjoint,
-            "serving": serving,
+            "kernels": kern, "ecc_eval_only": eval_only, "accuracy_vs_oracle": accuracy, "storage_forms": forms,
+            "adjoint_forms": adjoint, "serving": serving, "precision_c4": precision_c4,
             "total": result_total,
             "geometry_precision": "f64 per-view/per-pair set-up, double-float (~48-bit) tile anchors, f32 per-sample"}
     print(json.dumps(line), flush=True)

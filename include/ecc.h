@@ -307,6 +307,15 @@ int ecc_poll(ecc_ctx* ctx, uint64_t ticket, ecc_result* out);
  * jobs in them, the largest round, and the line-pair samples of completed jobs. */
 int ecc_serve_stats(ecc_ctx* ctx, long long* rounds, long long* job_rounds, int* max_batch, long long* line_pairs);
 
+/* Serving device time since the first ecc_submit, in milliseconds, from CUDA events
+ * on the scheduler's streams: the admissions' input copies (host to device), their
+ * dRadon/ds precomputes (with the view set-up), and the rounds (every launch of a
+ * round, from its first copy to its last kernel).  A round is counted once it has
+ * completed and the scheduler has seen it; with no job in flight the sums are complete.
+ * Admissions run on their own stream and overlap the rounds, so the sums may exceed
+ * the wall time. */
+int ecc_serve_times(ecc_ctx* ctx, double* upload_ms, double* precompute_ms, double* round_ms);
+
 /*
  * Allocation-free ecc_evaluate.  The paper has no counterpart: this is a service of
  * the library, not a step of the method.  It computes exactly what ecc_evaluate

@@ -24,7 +24,7 @@ from . import build as _build
 __all__ = ["EccError", "Context", "library_path", "load", "ecc_precompute_radon_derivative", "ecc_evaluate",
            "ecc_evaluate_grad", "ecc_evaluate_grad_projection", "ecc_evaluate_frozen", "ecc_evaluate_noalloc", "consistency",
            "ecc_scan_consistency_host", "ecc_status", "ecc_kernel_launches", "ecc_profile_enable",
-           "ecc_profile_read", "ecc_job_footprint", "ecc_submit", "ecc_poll", "ecc_serve_stats",
+           "ecc_profile_read", "ecc_job_footprint", "ecc_submit", "ecc_poll", "ecc_serve_stats", "ecc_serve_times",
            "ECC_F32", "ECC_F16", "ECC_BF16"]
 
 ECC_F32, ECC_F16, ECC_BF16 = 0, 1, 2
@@ -112,6 +112,8 @@ def load(build_if_missing: bool = True):
         lib.ecc_serve_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                         ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong)]
         lib.ecc_serve_stats.restype = i
+        lib.ecc_serve_times.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d)]
+        lib.ecc_serve_times.restype = i
         _lib = lib
         return lib
 
@@ -552,3 +554,11 @@ def ecc_serve_stats(ctx: Context) -> dict:
                                 ctypes.byref(lp))
     _check(ctx, rc, "ecc_serve_stats")
     return {"rounds": rounds.value, "job_rounds": job_rounds.value, "max_batch": mb.value, "line_pairs": lp.value}
+
+
+def ecc_serve_times(ctx: Context) -> dict:
+    """Serving device time [ms]: input uploads, precomputes and rounds (CUDA events)."""
+    up, pre, rnd = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+    rc = load().ecc_serve_times(ctx.handle, ctypes.byref(up), ctypes.byref(pre), ctypes.byref(rnd))
+    _check(ctx, rc, "ecc_serve_times")
+    return {"upload_ms": up.value, "precompute_ms": pre.value, "round_ms": rnd.value}

@@ -619,6 +619,18 @@ int ecc_serve_stats(ecc_ctx* c, long long* rounds, long long* job_rounds, int* m
   return ECC_OK;
 }
 
+int ecc_serve_times(ecc_ctx* c, double* upload_ms, double* precompute_ms, double* round_ms) {
+  if (!c) return fail(nullptr, ECC_EINVAL, "ctx is NULL");
+  if (!c->serve) {
+    if (upload_ms) *upload_ms = 0.0;
+    if (precompute_ms) *precompute_ms = 0.0;
+    if (round_ms) *round_ms = 0.0;
+    return ECC_OK;
+  }
+  ecc::serve_times(c->serve, upload_ms, precompute_ms, round_ms);
+  return ECC_OK;
+}
+
 }  // extern "C"
 
 // Internal (tests and diagnostics only, not part of the public ABI): copies the

@@ -143,6 +143,12 @@ struct ecc_serve {
   ecc::ServeJob* h_jobs[2] = {nullptr, nullptr};
   long long* h_off[2] = {nullptr, nullptr};
   cudaEvent_t round_ev[2] = {nullptr, nullptr};
+  // device time: timing events around each round (one pair per ring slot, read once
+  // the slot's round has completed) and around each admission's copies and precompute
+  cudaEvent_t round_t0[2] = {nullptr, nullptr}, round_t1[2] = {nullptr, nullptr};
+  bool round_pending[2] = {false, false};
+  cudaEvent_t admit_t[3] = {nullptr, nullptr, nullptr};
+  double round_ms = 0.0, upload_ms = 0.0, precompute_ms = 0.0;
   int pair_grid = 0;
   // pinned result slots
   unsigned char* slots = nullptr;
@@ -179,6 +185,7 @@ bool admit_job(ecc_serve* S, Job* J) {
   const size_t n = (size_t)d.n_views;
   unsigned char* R = J->dev;
   unsigned char* T = J->tmp;
+  cudaEventRecord(S->admit_t[0], s);
   e = cudaMemcpyAsync(R + L.P, d.P, n * 12 * sizeof(double), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {
     if (d.motion0)
@@ -201,6 +208,7 @@ bool admit_job(ecc_serve* S, Job* J) {
     set_err(J, ECC_ECUDA, cuda_msg("input copy", e));
     return false;
   }
+  cudaEventRecord(S->admit_t[1], s);
   ecc::view_setup_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(
       (int)n, (const double*)(R + L.P), nullptr, d.W, d.H, (ecc::ViewRec*)(R + L.views), (int*)(R + L.status));
   ecc::alpha_dir_kernel<<<(d.n_alpha + 255) / 256, 256, 0, s>>>(d.n_alpha, (float4*)(R + L.adir));
@@ -215,12 +223,20 @@ bool admit_job(ecc_serve* S, Job* J) {
     set_err(J, ECC_ECUDA, cuda_msg("precompute launch", e));
     return false;
   }
+  cudaEventRecord(S->admit_t[2], s);
   e = cudaFreeAsync(J->tmp, s);
   J->tmp = nullptr;
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     set_err(J, ECC_ECUDA, cuda_msg("precompute", e));
     return false;
+  }
+  float up = 0.0f, pre = 0.0f;
+  if (cudaEventElapsedTime(&up, S->admit_t[0], S->admit_t[1]) == cudaSuccess &&
+      cudaEventElapsedTime(&pre, S->admit_t[1], S->admit_t[2]) == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->upload_ms += up;
+    S->precompute_ms += pre;
   }
   return true;
 }
@@ -338,6 +354,14 @@ void round_loop(ecc_serve* S) {
     for (Job* J : S->ready) active.push_back(J);
     S->ready.clear();
     if (active.empty()) {
+      for (int b = 0; b < 2; ++b)  // no round in flight: account the last ones
+        if (S->round_pending[b] && finishing.empty()) {
+          float ms = 0.0f;
+          if (cudaEventSynchronize(S->round_t1[b]) == cudaSuccess &&
+              cudaEventElapsedTime(&ms, S->round_t0[b], S->round_t1[b]) == cudaSuccess)
+            S->round_ms += ms;
+          S->round_pending[b] = false;
+        }
       if (S->stop && finishing.empty()) return;
       if (finishing.empty())
         S->cv_round.wait(lk, [&] { return S->stop || !S->ready.empty(); });
@@ -360,6 +384,14 @@ void round_loop(ecc_serve* S) {
     // ---- one round over the active jobs
     const int b = (int)(round & 1);
     if (round >= 2) cudaEventSynchronize(S->round_ev[b]);  // the pinned copy of round - 2 is consumed
+    if (S->round_pending[b]) {  // its timing events are complete too
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, S->round_t0[b], S->round_t1[b]) == cudaSuccess) {
+        std::lock_guard<std::mutex> g(S->mu);
+        S->round_ms += ms;
+      }
+      S->round_pending[b] = false;
+    }
     const int nj = (int)active.size();
     ecc::ServeJob* H = S->h_jobs[b];
     long long* voff = S->h_off[b];
@@ -420,6 +452,7 @@ void round_loop(ecc_serve* S) {
     long long* dvoff = S->d_off + (size_t)b * 3 * (kMaxActive + 1);
     long long* dpoff = dvoff + (kMaxActive + 1);
     long long* dboff = dpoff + (kMaxActive + 1);
+    cudaEventRecord(S->round_t0[b], s);
     cudaError_t e = cudaMemcpyAsync(dj, H, sizeof(ecc::ServeJob) * nj, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(dvoff, voff, sizeof(long long) * 3 * (kMaxActive + 1), cudaMemcpyHostToDevice, s);
@@ -427,8 +460,10 @@ void round_loop(ecc_serve* S) {
     if (e == cudaSuccess) e = ecc::launch_serve_setup(dj, dvoff, dpoff, nj, voff[nj], poff[nj], s);
     if (e == cudaSuccess) e = ecc::launch_serve_pairs(dj, dboff, nj, S->d_counter + b, S->pair_grid, s);
     if (e == cudaSuccess) e = ecc::launch_serve_grad(dj, dvoff, dpoff, nj, voff[nj], poff[nj], s);
+    if (e == cudaSuccess) e = cudaEventRecord(S->round_t1[b], s);
     if (e == cudaSuccess) e = cudaEventRecord(S->round_ev[b], s);
     lk.lock();
+    S->round_pending[b] = e == cudaSuccess;
     ++S->n_rounds;
     S->job_rounds += nj;
     S->max_batch = std::max(S->max_batch, nj);
@@ -528,7 +563,10 @@ ecc_serve* serve_create(int device, size_t budget, std::string* why) {
     e = cudaMallocHost(&S->h_jobs[b], sizeof(ServeJob) * kMaxActive);
     if (e == cudaSuccess) e = cudaMallocHost(&S->h_off[b], sizeof(long long) * 3 * (kMaxActive + 1));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->round_ev[b], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&S->round_t0[b]);
+    if (e == cudaSuccess) e = cudaEventCreate(&S->round_t1[b]);
   }
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreate(&S->admit_t[k]);
   if (e == cudaSuccess) e = cudaMallocHost(&S->slots, kSlotBytes * kMaxActive);
   int sms = 0;
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
@@ -571,7 +609,11 @@ void serve_destroy(ecc_serve* S) {
     if (S->h_jobs[b]) cudaFreeHost(S->h_jobs[b]);
     if (S->h_off[b]) cudaFreeHost(S->h_off[b]);
     if (S->round_ev[b]) cudaEventDestroy(S->round_ev[b]);
+    if (S->round_t0[b]) cudaEventDestroy(S->round_t0[b]);
+    if (S->round_t1[b]) cudaEventDestroy(S->round_t1[b]);
   }
+  for (int k = 0; k < 3; ++k)
+    if (S->admit_t[k]) cudaEventDestroy(S->admit_t[k]);
   if (S->slots) cudaFreeHost(S->slots);
   if (S->s_admit) cudaStreamDestroy(S->s_admit);
   if (S->s_round) cudaStreamDestroy(S->s_round);
@@ -628,6 +670,13 @@ int serve_poll(ecc_serve* S, uint64_t ticket, ecc_result* out, std::string* why)
   S->jobs.erase(it);
   delete J;
   return r.status;
+}
+
+void serve_times(ecc_serve* S, double* upload_ms, double* precompute_ms, double* round_ms) {
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (upload_ms) *upload_ms = S->upload_ms;
+  if (precompute_ms) *precompute_ms = S->precompute_ms;
+  if (round_ms) *round_ms = S->round_ms;
 }
 
 void serve_stats(ecc_serve* S, long long* rounds, long long* job_rounds, int* max_batch, long long* line_pairs) {

@@ -20,5 +20,6 @@ void serve_destroy(ecc_serve* s);
 int serve_submit(ecc_serve* s, const ecc_job* job, uint64_t* ticket, std::string* why);
 int serve_poll(ecc_serve* s, uint64_t ticket, ecc_result* out, std::string* why);
 void serve_stats(ecc_serve* s, long long* rounds, long long* job_rounds, int* max_batch, long long* line_pairs);
+void serve_times(ecc_serve* s, double* upload_ms, double* precompute_ms, double* round_ms);
 
 }  // namespace ecc

@@ -24,7 +24,7 @@ if mode == "max":
     print(json.dumps({{"rank": rank, "world": world, "max": got}}), flush=True)
     pg.destroy_process_group()
 else:
-    sys.argv = ["bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0"]
+    sys.argv = ["bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0", "--ref-stride", "62"]
     sys.exit(bench.main())
 """
 
