@@ -69,3 +69,19 @@ def p_entry_scale(P):
     s[:, :, :3] = np.abs(P[:, :, :3]).max(axis=2, keepdims=True)
     s[:, :, 3] = np.abs(P[:, :, 3]) + 100.0 * s[:, :, 0]
     return s.reshape(-1, 12)
+
+
+def round_bf16(x):
+    """Round to the nearest BF16 value (8 significant bits, ties to even), in FP64."""
+    m, e = np.frexp(np.asarray(x, dtype=np.float64))   # x = m 2^e, 1/2 <= |m| < 1
+    return np.ldexp(np.round(m * 256.0) / 256.0, e)
+
+
+def quantize_f16(S):
+    """FP16 storage with a per-view scale, as the precompute defines it: scale =
+    max|S| / 2^14 of each view (FP32; 1 for an all-zero view), stored value =
+    S / scale rounded to FP16.  Returns (stored FP16 array, FP32 scales)."""
+    S = np.asarray(S, dtype=np.float64)
+    amax = np.abs(S).reshape(S.shape[0], -1).max(axis=1).astype(np.float32)
+    scales = np.where(amax > 0, amax / np.float32(16384.0), np.float32(1.0)).astype(np.float32)
+    return (S / scales.astype(np.float64)[:, None, None]).astype(np.float16), scales

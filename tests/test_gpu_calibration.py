@@ -22,8 +22,10 @@ from tests import helpers as H
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-# same bar as the motion gradient: relative L2 error of the whole (scaled) gradient
-TOL_GRAD = 1e-4
+# the FP32 bar, as for the motion gradient: relative L2 error of the whole (scaled)
+# gradient, and every component within TOL_GRAD of its norm.  Measured (GB300): 1.0e-7
+# (c = 0) and 1.9e-7 (Cauchy c = median d) on the 20-view subset.
+TOL_GRAD = 1e-5
 VIEWS = tuple(range(0, 248, 13))   # 20 views of the 248-view motion workload
 
 
@@ -79,8 +81,9 @@ def test_grad_P_matches_oracle(c):
     s = H.p_entry_scale(sc["P"])
     gs, rs = g * s, ref["grad"] * s
     err = np.linalg.norm(gs - rs) / np.linalg.norm(rs)
-    assert err <= TOL_GRAD, err
-    assert np.abs(gs - rs).max() <= 10 * TOL_GRAD * np.abs(rs).max()
+    comp = np.abs(gs - rs).max() / np.linalg.norm(rs)
+    print(f"calibration gradient vs oracle, c = {c}: rel L2 {err:.2e}, max component / norm {comp:.2e}")
+    assert err <= TOL_GRAD and comp <= TOL_GRAD, (err, comp)
     assert abs(total - ref["total"]) <= H.TOL_F32 * ref["total"]
 
 
@@ -93,7 +96,10 @@ def test_grad_P_explicit_pairs():
     _, g = _gpu_grad_P(sc["P"], S32, cfg.W, cfg.H, cfg.K, pairs=pairs)
     ref = orc.ecc_grad_P(sc["P"], S32.astype(np.float64), cfg.W, cfg.H, cfg.K, pairs=pairs)
     s = H.p_entry_scale(sc["P"])
-    assert np.linalg.norm((g - ref["grad"]) * s) <= TOL_GRAD * np.linalg.norm(ref["grad"] * s)
+    err = np.linalg.norm((g - ref["grad"]) * s) / np.linalg.norm(ref["grad"] * s)
+    comp = np.abs((g - ref["grad"]) * s).max() / np.linalg.norm(ref["grad"] * s)
+    print(f"calibration gradient vs oracle, explicit pairs: rel L2 {err:.2e}, max component / norm {comp:.2e}")
+    assert err <= TOL_GRAD and comp <= TOL_GRAD, (err, comp)
 
 
 def test_grad_P_euler_identity_and_motion_gradient():

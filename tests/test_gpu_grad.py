@@ -14,10 +14,18 @@ from tests import helpers as H
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-# gradient parity: relative L2 error of the whole gradient; FP32 per-sample terms
-# and the rare bilinear-cell choices at grid lines (the slopes are cell-wise
-# constant) bound it
-TOL_GRAD = 1e-4
+# gradient parity at the FP32 bar: relative L2 error of the whole gradient, and every
+# component within TOL_GRAD of the gradient's norm.  Measured (GB300): c1 1.6e-7, the
+# 20-view subset 7.0e-7 (c = 0) and 8.9e-7 (Cauchy c = median d), opposed full-scan
+# views at K = 77 8.3e-7, an explicit pair list 2.5e-6, the full-size rows below
+# (printed by the test).
+TOL_GRAD = 1e-5
+
+
+def grad_errors(g, ref):
+    """Relative L2 error, and the largest component error relative to the norm."""
+    nrm = np.linalg.norm(ref)
+    return np.linalg.norm(g - ref) / nrm, np.abs(g - ref).max() / nrm
 
 
 @functools.lru_cache(maxsize=None)
@@ -58,9 +66,9 @@ def test_grad_matches_oracle(c):
         c = float(np.median(orc.ecc(sc["P"], S32.astype(np.float64), cfg.W, cfg.H, cfg.K, motion=th)["d"]))
     total, g, _ = _gpu_grad(sc["P"], S32, cfg.W, cfg.H, cfg.K, c, th)
     ref = orc.ecc_grad(sc["P"], S32.astype(np.float64), cfg.W, cfg.H, cfg.K, cauchy_c=c, motion=th)
-    err = np.linalg.norm(g - ref["grad"]) / np.linalg.norm(ref["grad"])
-    assert err <= TOL_GRAD, err
-    assert np.abs(g - ref["grad"]).max() <= 10 * TOL_GRAD * np.abs(ref["grad"]).max()
+    err, comp = grad_errors(g, ref["grad"])
+    print(f"gradient vs oracle, 20 views, c = {c}: rel L2 {err:.2e}, max component / norm {comp:.2e}")
+    assert err <= TOL_GRAD and comp <= TOL_GRAD, (err, comp)
     assert abs(total - ref["total"]) <= H.TOL_F32 * ref["total"]
 
 
@@ -77,8 +85,9 @@ def test_grad_full_scan_opposed_views_ragged_tiles():
     total, g, _ = _gpu_grad(sc["P"], S32, cfg.W, cfg.H, 77, 0.0, th)
     ref = orc.ecc_grad(sc["P"], S32.astype(np.float64), cfg.W, cfg.H, 77, motion=th)
     assert (ref["arcs"][:, 2] > 3.14).any()
-    err = np.linalg.norm(g - ref["grad"]) / np.linalg.norm(ref["grad"])
-    assert err <= TOL_GRAD, err
+    err, comp = grad_errors(g, ref["grad"])
+    print(f"gradient vs oracle, opposed views, K = 77: rel L2 {err:.2e}, max component / norm {comp:.2e}")
+    assert err <= TOL_GRAD and comp <= TOL_GRAD, (err, comp)
     assert abs(total - ref["total"]) <= H.TOL_F32 * ref["total"]
 
 
@@ -91,7 +100,9 @@ def test_grad_explicit_pairs_and_zero_motion():
     th = np.zeros((n, 6))
     total, g, _ = _gpu_grad(sc["P"], S32, cfg.W, cfg.H, cfg.K, 0.0, th, pairs)
     ref = orc.ecc_grad(sc["P"], S32.astype(np.float64), cfg.W, cfg.H, cfg.K, motion=th, pairs=pairs)
-    assert np.linalg.norm(g - ref["grad"]) <= TOL_GRAD * np.linalg.norm(ref["grad"])
+    err, comp = grad_errors(g, ref["grad"])
+    print(f"gradient vs oracle, explicit pairs: rel L2 {err:.2e}, max component / norm {comp:.2e}")
+    assert err <= TOL_GRAD and comp <= TOL_GRAD, (err, comp)
 
 
 def test_grad_vs_central_differences_of_frozen_forward():
@@ -163,26 +174,30 @@ def test_autograd_function():
 def test_c3_full_size_gradient():
     """The differentiation workload at full size: 248 views, seeded rigid motion (rotations
     N(0, 1 deg), translations N(0, 2 mm)), all 30,628 pairs, K = 512.
-    * Three sampled views' gradient rows against the oracle's complex-step gradient over all pairs
-      that contain them, on the library's own sinograms.
-    * Central differences of the frozen forward, h = 1e-4 on 32 random parameters."""
+    * On the oracle's sinograms (rounded to FP32): three sampled views' gradient rows against
+      the oracle's complex-step gradient over all pairs that contain them, at the FP32 bar.
+    * On the library's own sinograms: central differences of the frozen forward, h = 1e-4 on
+      32 random parameters."""
     import paper_1806_02637_gb300 as ecc
     cfg = synth.CONFIGS["c3"]
     sc = H.scan("c3")
     n = cfg.n_views
     th = sc["motion"]
     P = _cuda(sc["P"])
+    S_or = H.oracle_sino("c3").astype(np.float32)
+    r = ecc.ecc_evaluate_grad(_ctx(), P, _cuda(S_or), cfg.W, cfg.H, cfg.K, motion=_cuda(th))
+    g = r["grad"].cpu().numpy()
+    views = sorted(int(v) for v in np.random.default_rng(248).choice(n, 3, replace=False))
+    pairs = np.array(sorted({(min(a, b), max(a, b)) for a in views for b in range(n) if b != a}), dtype=np.int32)
+    ref = orc.ecc_grad(sc["P"], S_or.astype(np.float64), cfg.W, cfg.H, cfg.K, motion=th, pairs=pairs)
+    for v in views:
+        err, comp = grad_errors(g[v], ref["grad"][v])
+        print(f"gradient vs oracle, full size, view {v}: rel L2 {err:.2e}, max component / norm {comp:.2e}")
+        assert err <= TOL_GRAD and comp <= TOL_GRAD, (v, err, comp)
     S, _ = ecc.ecc_precompute_radon_derivative(_ctx(), P, _cuda(sc["images"]), cfg.n_alpha, cfg.n_s)
     r = ecc.ecc_evaluate_grad(_ctx(), P, S, cfg.W, cfg.H, cfg.K, motion=_cuda(th))
     g = r["grad"].cpu().numpy()
     total = float(r["total"].cpu()[0])
-    S64 = S.cpu().numpy().astype(np.float64)
-    views = sorted(int(v) for v in np.random.default_rng(248).choice(n, 3, replace=False))
-    pairs = np.array(sorted({(min(a, b), max(a, b)) for a in views for b in range(n) if b != a}), dtype=np.int32)
-    ref = orc.ecc_grad(sc["P"], S64, cfg.W, cfg.H, cfg.K, motion=th, pairs=pairs)
-    for v in views:
-        err = np.linalg.norm(g[v] - ref["grad"][v]) / np.linalg.norm(ref["grad"][v])
-        assert err <= TOL_GRAD, (v, err)
     # central differences of the library's frozen forward at the configuration's h = 1e-4.
     # Most components agree to the bilinear-kink level; a few are dominated by one pair
     # whose dependence is steep on a scale below 1e-6 rad (the oracle's own FP64
