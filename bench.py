@@ -415,6 +415,21 @@ def run_reference(args):
     return 0
 
 
+def wall_ms(fn, reps):
+    """Mean time of fn() over reps calls, CUDA events on the current stream around the
+    calls (the pair set-up of later pair chunks overlaps earlier chunks' pair kernels on
+    a second stream, so summed kernel times overstate a call)."""
+    import torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(reps):
+        fn()
+    ev1.record()
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / reps
+
+
 # ------------------------------------------------------------------ storage forms
 def storage_forms(ctx, P, images, cfg, total_f32, reps=10, oracle=None, l2_gbs=None):
     """The reduced-precision form: the same scan's sinograms stored in FP16 (per-view
@@ -442,9 +457,9 @@ def storage_forms(ctx, P, images, cfg, total_f32, reps=10, oracle=None, l2_gbs=N
         torch.cuda.synchronize()
         prof = ecc.ecc_profile_read(ctx)
         ecc.ecc_profile_enable(ctx, False)
-        eval_ms = sum(prof[n][1] for n in ("alpha_dir_kernel", "pair_setup_kernel", "ecc_pair_kernel",
-                                           "reduce_kernel") if n in prof) / reps
-        pk_ms = prof["ecc_pair_kernel"][1] / prof["ecc_pair_kernel"][0]
+        eval_ms = wall_ms(lambda: ecc.ecc_evaluate(ctx, P, S, cfg.W, cfg.H, cfg.K, scales=scales, total=tot,
+                                                   want_per_pair=False), reps)
+        pk_ms = prof["ecc_pair_kernel"][1] / reps   # all chunks of one evaluation
         gbs = 16.0 * units / (pk_ms / 1e3) / 1e9
         t = float(tot.cpu()[0])
         out[name] = {"ms_per_eval": eval_ms, "line_pairs_per_s": units / (eval_ms / 1e3), "pair_kernel_ms": pk_ms,
@@ -462,23 +477,23 @@ def storage_forms(ctx, P, images, cfg, total_f32, reps=10, oracle=None, l2_gbs=N
     return out
 
 
-def l2_read_rate(dev, mb=48, reps=200):
-    """Read rate of a buffer resident in L2 (48 MB of the 129 MB): torch.sum over it,
-    timed with CUDA events; the denominator of the L2 fractions."""
-    import torch
-    x = torch.ones((mb * (1 << 20)) // 4, dtype=torch.float32, device=dev)
-    for _ in range(10):
-        x.sum()
-    torch.cuda.synchronize(dev)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
-    for _ in range(reps):
-        x.sum()
-    ev1.record()
-    torch.cuda.synchronize(dev)
-    gbs = reps * x.numel() * 4 / (ev0.elapsed_time(ev1) / 1e3) / 1e9
-    del x
-    return {"gbs": gbs, "how": f"torch.sum over a resident {mb} MB FP32 buffer, {reps} times, CUDA events"}
+def l2_read_rate(dev, sizes_mb=(32, 64, 96), reps=200):
+    """Read rate of a buffer resident in L2 (129 MB), the denominator of the L2
+    fractions: the library's diagnostic read kernel (16-byte loads that skip L1, 8
+    blocks per SM), CUDA events around `reps` launches; the best of three sizes."""
+    import ctypes
+    import paper_1806_02637_gb300 as ecc
+    lib = ecc.load()
+    lib.ecc_internal_l2_read_rate.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    lib.ecc_internal_l2_read_rate.restype = ctypes.c_int
+    rates = {}
+    for mb in sizes_mb:
+        g = ctypes.c_double(0.0)
+        if lib.ecc_internal_l2_read_rate(ctypes.c_size_t(mb << 20), reps, ctypes.byref(g)) == 0:
+            rates[f"{mb}MB"] = g.value
+    best = max(rates.values()) if rates else float("nan")
+    return {"gbs": best, "by_size_gbs": rates,
+            "how": f"L2-resident buffers read with ld.global.cg float4, 8 blocks per SM, {reps} launches, CUDA events"}
 
 
 # ------------------------------------------------------------------ precision leg (1240-view scan)
@@ -541,9 +556,9 @@ def c4_leg(ctx, l2_gbs, reps=5):
         torch.cuda.synchronize()
         prof = ecc.ecc_profile_read(ctx)
         ecc.ecc_profile_enable(ctx, False)
-        eval_ms = sum(prof[n][1] for n in ("alpha_dir_kernel", "pair_setup_kernel", "ecc_pair_kernel",
-                                           "reduce_kernel") if n in prof) / reps
-        pk_ms = prof["ecc_pair_kernel"][1] / prof["ecc_pair_kernel"][0]
+        eval_ms = wall_ms(lambda: ecc.ecc_evaluate(ctx, P, S, cfg.W, cfg.H, cfg.K, scales=scales, total=tot,
+                                                   want_per_pair=False), reps)
+        pk_ms = prof["ecc_pair_kernel"][1] / reps   # all chunks of one evaluation
         gbs = 16.0 * units / (pk_ms / 1e3) / 1e9
         r = ecc.ecc_evaluate(ctx, P, S, cfg.W, cfg.H, cfg.K, scales=scales)
         d = r["per_pair"][:, 0].cpu().numpy()
@@ -595,7 +610,7 @@ def adjoint_forms(ctx, P, sino, cfg, reps=5):
         torch.cuda.synchronize()
         prof = ecc.ecc_profile_read(ctx)
         ecc.ecc_profile_enable(ctx, False)
-        ms = sum(t for _, t in prof.values()) / reps
+        ms = wall_ms(lambda: fn(ctx, P, sino, cfg.W, cfg.H, cfg.K, motion=motion, want_per_pair=False), reps)
         out[name] = {"ms_per_call": ms, "line_pairs_per_s": units / (ms / 1e3),
                      "kernels_ms": {k: t / reps for k, (c, t) in sorted(prof.items(), key=lambda kv: -kv[1][1])}}
     out["note"] = ("ecc_evaluate_grad / ecc_evaluate_grad_projection on the FP32 sinograms of this scan, seeded "
@@ -736,13 +751,14 @@ def run_ours(args):
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
                 "work": "32 B (2 views x 4 taps x FP32) per line-pair sample"}
     ev_names = ("view_setup_kernel", "alpha_dir_kernel", "pair_setup_kernel", "ecc_pair_kernel", "reduce_kernel")
-    eval_ms = sum(kern[n]["ms_per_step"] for n in ("alpha_dir_kernel", "pair_setup_kernel", "ecc_pair_kernel",
-                                                   "reduce_kernel") if n in kern)
+    eval_ms = wall_ms(lambda: ecc.ecc_evaluate(ctx, P, sino, cfg.W, cfg.H, cfg.K, total=total, want_per_pair=False),
+                      10)
     pk = kern.get("ecc_pair_kernel")
     eval_only = None
     if pk:
         gbs = 32.0 * units / (pk["ms_per_step"] / 1e3) / 1e9
-        eval_only = {"ms_per_step": eval_ms, "line_pairs_per_s": units / (eval_ms / 1e3),
+        eval_only = {"ms_per_eval": eval_ms, "line_pairs_per_s": units / (eval_ms / 1e3),
+                     "how": "ecc_evaluate alone on resident sinograms, 10 calls between CUDA events",
                      "pair_kernel_ms": pk["ms_per_step"],
                      "pair_kernel_gather_gbs": gbs,
                      "pair_kernel_frac_of_hbm": gbs / peaks.get("hbm_gbs", 6800.0),

@@ -188,7 +188,9 @@ static int SFX(view_setup_P)(const REAL Pm[12], SFX(view_t)* v) {
  * u = baseline direction, w = (up_a + up_b) made orthogonal to u, v = w x u.
  * The plane at angle kappa has normal n = cos(kappa) w + sin(kappa) v.
  * If up_a + up_b is (nearly) parallel to u, the world axis least aligned with u
- * replaces it.  Returns -1 if the two sources coincide. */
+ * replaces it: the first axis whose |u_i| is within 1e-9 of the smallest, so that
+ * axes tied in exact arithmetic (a baseline along the third axis: u_0 = u_1 = 0)
+ * are not told apart by rounding.  Returns -1 if the two sources coincide. */
 static int SFX(pair_frame)(const SFX(view_t)* va, const SFX(view_t)* vb, REAL w[3], REAL v[3]) {
     REAL d[3] = {vb->C[0] - va->C[0], vb->C[1] - va->C[1], vb->C[2] - va->C[2]};
     REAL nd = R_SQRT(SFX(dot3)(d, d));
@@ -199,10 +201,11 @@ static int SFX(pair_frame)(const SFX(view_t)* va, const SFX(view_t)* vb, REAL w[
     REAL wt[3] = {r[0] - ru * u[0], r[1] - ru * u[1], r[2] - ru * u[2]};
     REAL nw = R_SQRT(SFX(dot3)(wt, wt));
     if (RE(nw) < 1e-6) {
-        int ax = 0;
         double best = fabs(RE(u[0]));
         for (int i = 1; i < 3; ++i)
-            if (fabs(RE(u[i])) < best) { best = fabs(RE(u[i])); ax = i; }
+            if (fabs(RE(u[i])) < best) best = fabs(RE(u[i]));
+        int ax = 0;
+        while (fabs(RE(u[ax])) > best + 1e-9) ++ax;
         REAL ui = u[ax];
         for (int i = 0; i < 3; ++i) wt[i] = (i == ax ? 1.0 : 0.0) - ui * u[i];
         nw = R_SQRT(SFX(dot3)(wt, wt));

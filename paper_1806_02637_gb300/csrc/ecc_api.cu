@@ -50,6 +50,10 @@ struct ecc_ctx {
   const void* samp_pair_ptr = nullptr;
   Buf h_P, h_img, h_sino, h_total;  // buffers of the host-buffer entry point
   cudaStream_t copy_stream = nullptr;  // its image uploads, per precompute batch
+  // the pair set-up of chunk i + 1 runs on setup_stream while the pair kernel of chunk i
+  // runs on the caller's stream (FP64 set-up beside FP32 gathers on the same SMs)
+  cudaStream_t setup_stream = nullptr;
+  cudaEvent_t ev_views = nullptr, ev_chunk[8] = {};
   ecc_serve* serve = nullptr;       // serving scheduler, created by the first ecc_submit
 };
 
@@ -217,7 +221,7 @@ int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion,
   }
   const int n_tiles = (n_kappa + 31) / 32;
   const long long np = n_pairs;
-  const long long n_blocks = (np + 7) / 8;
+  const long long n_blocks = (np + 7) / 8 + 8;  // blocks of 8 or 16 pairs, over at most 8 chunks
   if ((rc = ensure(c, c->views, sizeof(ecc::ViewRec) * (size_t)n_views, "views")) != ECC_OK) return rc;
   if ((rc = ensure(c, c->pairs, sizeof(ecc::PairRec) * (size_t)np, "pairs")) != ECC_OK) return rc;
   if ((rc = ensure(c, c->ctile, sizeof(float4) * (size_t)np * n_tiles, "tile directions")) != ECC_OK) return rc;
@@ -250,18 +254,51 @@ int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion,
   ecc::alpha_dir_kernel<<<(n_alpha + 255) / 256, 256, 0, s>>>(n_alpha, (float4*)c->adir.p);
   hk.on_end("alpha_dir_kernel", s);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "alpha table launch");
-  hk.on_begin("pair_setup_kernel", s);
-  ecc::pair_setup_kernel<<<(unsigned)((np + 127) / 128), 128, 0, s>>>(
-      n_views, np, pairs, (const ecc::ViewRec*)c->views.p, W, H, n_kappa, (ecc::PairRec*)c->pairs.p,
-      (float4*)c->ctile.p, n_tiles, reuse ? 1 : 0, c->d_status);
-  hk.on_end("pair_setup_kernel", s);
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "pair set-up launch");
+  // Pairs in chunks: the FP64 set-up of chunk i + 1 (setup_stream) overlaps the pair
+  // kernel of chunk i (the caller's stream), which waits for its own chunk's set-up.
+  // A chunk keeps at least ecc::kPairsPerChunkMin pairs, enough for the forward
+  // kernel's two-pair blocks; small launches stay one chunk on one stream.
+  const int n_chunks = (int)std::max<long long>(1, std::min<long long>(8, np / ecc::pairs_per_chunk_min()));
+  if (n_chunks > 1 && !c->setup_stream) {
+    if ((e = cudaStreamCreateWithFlags(&c->setup_stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(c, e, "set-up stream");
+    if ((e = cudaEventCreateWithFlags(&c->ev_views, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(c, e, "event");
+    for (int i = 0; i < 8; ++i)
+      if ((e = cudaEventCreateWithFlags(&c->ev_chunk[i], cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(c, e, "event");
+  }
+  cudaStream_t ss = n_chunks > 1 ? c->setup_stream : s;
+  if (n_chunks > 1) {
+    if ((e = cudaEventRecord(c->ev_views, s)) != cudaSuccess) return cuda_fail(c, e, "event record");
+    if ((e = cudaStreamWaitEvent(ss, c->ev_views, 0)) != cudaSuccess) return cuda_fail(c, e, "stream wait");
+  }
+  long long chunk_beg[9];
+  for (int i = 0; i <= n_chunks; ++i) chunk_beg[i] = np * i / n_chunks;
+  for (int i = 0; i < n_chunks; ++i) {
+    const long long p0 = chunk_beg[i], p1 = chunk_beg[i + 1];
+    hk.on_begin("pair_setup_kernel", ss);
+    ecc::pair_setup_kernel<<<(unsigned)((p1 - p0 + 127) / 128), 128, 0, ss>>>(
+        n_views, p0, p1, pairs, (const ecc::ViewRec*)c->views.p, W, H, n_kappa, (ecc::PairRec*)c->pairs.p,
+        (float4*)c->ctile.p, n_tiles, reuse ? 1 : 0, c->d_status);
+    hk.on_end("pair_setup_kernel", ss);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "pair set-up launch");
+    if (n_chunks > 1 && (e = cudaEventRecord(c->ev_chunk[i], ss)) != cudaSuccess) return cuda_fail(c, e, "event");
+  }
   int nb = 0;
-  e = ecc::launch_ecc_pairs(np, (const ecc::PairRec*)c->pairs.p, (const float4*)c->ctile.p, n_tiles,
-                            (const float4*)c->adir.p, sino, scales, dtype, n_alpha, n_s, n_kappa, W, H, cauchy_c,
-                            per_pair, nkappa, (double*)c->partial.p, (grad || grad_P) ? (double*)c->Gpp.p : nullptr,
-                            c->d_status, &nb, hk, s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "pair kernel launch");
+  double* Gpp = (grad || grad_P) ? (double*)c->Gpp.p : nullptr;
+  for (int i = 0; i < n_chunks; ++i) {
+    const long long p0 = chunk_beg[i], p1 = chunk_beg[i + 1];
+    if (n_chunks > 1 && (e = cudaStreamWaitEvent(s, c->ev_chunk[i], 0)) != cudaSuccess)
+      return cuda_fail(c, e, "stream wait");
+    int nbi = 0;
+    e = ecc::launch_ecc_pairs(p1 - p0, (const ecc::PairRec*)c->pairs.p + p0, (const float4*)c->ctile.p + p0 * n_tiles,
+                              n_tiles, (const float4*)c->adir.p, sino, scales, dtype, n_alpha, n_s, n_kappa, W, H,
+                              cauchy_c, per_pair + 2 * p0, nkappa ? nkappa + p0 : nullptr,
+                              (double*)c->partial.p + nb, Gpp ? Gpp + 12 * p0 : nullptr, c->d_status, &nbi, hk, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pair kernel launch");
+    nb += nbi;
+  }
   e = ecc::launch_reduce((const double*)c->partial.p, nb, total, hk, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "reduce launch");
   if (grad || grad_P) {
@@ -356,6 +393,10 @@ void ecc_destroy(ecc_ctx* c) {
   }
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  if (c->setup_stream) cudaStreamDestroy(c->setup_stream);
+  if (c->ev_views) cudaEventDestroy(c->ev_views);
+  for (cudaEvent_t ev : c->ev_chunk)
+    if (ev) cudaEventDestroy(ev);
   delete c;
 }
 

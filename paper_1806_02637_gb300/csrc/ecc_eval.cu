@@ -909,13 +909,17 @@ __device__ __forceinline__ double pair_warp_adjoint(const PairArgs& g, long long
                : tile_adjoint_general_body<T>(recw + kRec * tt, recw + kRec * (16 + tt), q, sa, sb, sca, scb, n_alpha,
                                               n_s, inv_dalpha, inv_ds_f, Af, ckx, cky, ga, gb);
       acc += valid ? dd * dd : 0.0f;
-      const float w2 = valid ? 2.0f * dd : 0.0f;
+      // masked samples may sit anywhere (their slopes need not be finite): skipped, not
+      // multiplied by zero
+      if (valid) {
+        const float w2 = 2.0f * dd;
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        G[2 * i] = fmaf(w2 * ga[i], ckx, G[2 * i]);
-        G[2 * i + 1] = fmaf(w2 * ga[i], cky, G[2 * i + 1]);
-        G[6 + 2 * i] = fmaf(-w2 * gb[i], ckx, G[6 + 2 * i]);
-        G[6 + 2 * i + 1] = fmaf(-w2 * gb[i], cky, G[6 + 2 * i + 1]);
+        for (int i = 0; i < 3; ++i) {
+          G[2 * i] = fmaf(w2 * ga[i], ckx, G[2 * i]);
+          G[2 * i + 1] = fmaf(w2 * ga[i], cky, G[2 * i + 1]);
+          G[6 + 2 * i] = fmaf(-w2 * gb[i], ckx, G[6 + 2 * i]);
+          G[6 + 2 * i + 1] = fmaf(-w2 * gb[i], cky, G[6 + 2 * i + 1]);
+        }
       }
     };
     for (int t0 = 0; t0 < n_tiles; t0 += 16) {
@@ -1130,6 +1134,13 @@ cudaError_t launch_ecc_pairs(long long n_pairs, const PairRec* prs, const float4
 #undef ECC_LAUNCH
   hooks.on_end(name, stream);
   return cudaGetLastError();
+}
+
+long long pairs_per_chunk_min() {
+  int dev = 0, n_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    n_sm = 1;
+  return (long long)kPairsPerForwardBlock * 4 * n_sm * kForwardWavesForTwo;
 }
 
 int serve_pairs_blocks_per_sm() {

@@ -128,7 +128,7 @@ extern "C" int ecc_evaluate_noalloc(int n_views, const double* P, const double* 
   const ecc::LaunchHooks hk;  // no context: nothing to count or time
   ecc::view_setup_kernel<<<(n_views + 127) / 128, 128, 0, s>>>(n_views, P, motion, W, H, views, status);
   ecc::alpha_dir_kernel<<<(n_alpha + 255) / 256, 256, 0, s>>>(n_alpha, adir);
-  ecc::pair_setup_kernel<<<(n_pairs + 127) / 128, 128, 0, s>>>(n_views, n_pairs, pairs, views, W, H, n_kappa, prs,
+  ecc::pair_setup_kernel<<<(n_pairs + 127) / 128, 128, 0, s>>>(n_views, 0, n_pairs, pairs, views, W, H, n_kappa, prs,
                                                                ctile, n_tiles, 0, status);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail(ECC_ECUDA, cudaGetErrorString(e));
   int nb = 0;

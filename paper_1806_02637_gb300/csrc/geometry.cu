@@ -121,13 +121,10 @@ __host__ __device__ bool pencil_frame(const T* Ca, const T* Cb, const T* upa, co
   for (int k = 0; k < 3; ++k) w[k] = rr[k] - ru * u[k];
   T nw = sqrt(dot3(w, w));
   if (value(nw) < 1e-6) {
+    // the first axis within 1e-9 of the smallest |u_k|: ties are not left to rounding
+    const double best = fmin(fabs(value(u[0])), fmin(fabs(value(u[1])), fabs(value(u[2]))));
     int ax = 0;
-    double best = fabs(value(u[0]));
-    for (int k = 1; k < 3; ++k)
-      if (fabs(value(u[k])) < best) {
-        best = fabs(value(u[k]));
-        ax = k;
-      }
+    while (fabs(value(u[ax])) > best + 1e-9) ++ax;
     const T ui = u[ax];
     for (int k = 0; k < 3; ++k) w[k] = T(k == ax ? 1.0 : 0.0) - ui * u[k];
     nw = sqrt(dot3(w, w));
@@ -158,13 +155,9 @@ __host__ __device__ bool pencil_frame_adjoint(const double* Ca, const double* Cb
   double nw = sqrt(dot3(wt, wt));
   int ax = -1;
   if (nw < 1e-6) {
+    const double best = fmin(fabs(u[0]), fmin(fabs(u[1]), fabs(u[2])));
     ax = 0;
-    double best = fabs(u[0]);
-    for (int k = 1; k < 3; ++k)
-      if (fabs(u[k]) < best) {
-        best = fabs(u[k]);
-        ax = k;
-      }
+    while (fabs(u[ax]) > best + 1e-9) ++ax;
     const double ui = u[ax];
     for (int k = 0; k < 3; ++k) wt[k] = (k == ax ? 1.0 : 0.0) - ui * u[k];
     nw = sqrt(dot3(wt, wt));
@@ -476,12 +469,12 @@ __host__ __device__ PairRec setup_pair(int a, int b, int n_views, const ViewRec*
   return r;
 }
 
-__global__ void pair_setup_kernel(int n_views, long long n_pairs, const int32_t* __restrict__ pairs,
+__global__ void pair_setup_kernel(int n_views, long long p_begin, long long p_end, const int32_t* __restrict__ pairs,
                                   const ViewRec* __restrict__ views, int W, int H, int K,
                                   PairRec* __restrict__ out, float4* __restrict__ ctile, int n_tiles,
                                   int reuse_sampling, int* __restrict__ status) {
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n_pairs) return;
+  const long long p = p_begin + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= p_end) return;
   int a, b;
   if (pairs) {
     a = pairs[2 * p];

@@ -9,9 +9,10 @@ namespace ecc {
 
 __global__ void view_setup_kernel(int n_views, const double* P, const double* motion, int W, int H, ViewRec* out,
                                   int* status);
-__global__ void pair_setup_kernel(int n_views, long long n_pairs, const int32_t* pairs, const ViewRec* views, int W,
-                                  int H, int K, PairRec* out, float4* ctile, int n_tiles, int reuse_sampling,
-                                  int* status);
+// pairs [p_begin, p_end) of the row-major a < b enumeration (pairs == NULL) or of the list
+__global__ void pair_setup_kernel(int n_views, long long p_begin, long long p_end, const int32_t* pairs,
+                                  const ViewRec* views, int W, int H, int K, PairRec* out, float4* ctile, int n_tiles,
+                                  int reuse_sampling, int* status);
 __global__ void view_tangent_kernel(int n_views, const double* P, const double* motion, int W, int H, ViewTan* out);
 __global__ void view_grad_theta_kernel(int n_views, long long n_pairs, const int32_t* pairs, const double* gq,
                                        const ViewTan* vtan, double* grad);
@@ -96,6 +97,10 @@ size_t radon_f16_stage_bytes(int n_alpha, int n_s, int batch_views);
 int radon_pad(int W, int H, int n_s);
 // Bytes of one view's weighted-image planes (interpolation pairs, both orientations).
 size_t radon_plane_bytes(int W, int H, int n_s);
+
+// Smallest number of pairs per pair-kernel launch that keeps the forward kernel's
+// two-pair blocks (several waves of them on this device).
+long long pairs_per_chunk_min();
 
 cudaError_t launch_ecc_pairs(long long n_pairs, const PairRec* prs, const float4* ctile, int n_tiles,
                              const float4* alpha_dir, const void* sino, const float* scales, int dtype,

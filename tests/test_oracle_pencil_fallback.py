@@ -53,12 +53,12 @@ def _data():
 
 
 def np_fallback_frame(Pa, Pb):
-    """The rule restated: u = baseline direction; the first axis of smallest |u_i|
-    minus its projection on u, normalised, is w; v = w x u."""
+    """The rule restated: u = baseline direction; the first axis whose |u_i| is within
+    1e-9 of the smallest, minus its projection on u, normalised, is w; v = w x u."""
     _, _, Ca, _ = _np_view(Pa)
     _, _, Cb, _ = _np_view(Pb)
     u = (Cb - Ca) / np.linalg.norm(Cb - Ca)
-    ax = int(np.argmin(np.abs(u)))        # argmin returns the first of equal values
+    ax = int(np.nonzero(np.abs(u) <= np.abs(u).min() + 1e-9)[0][0])
     e = np.zeros(3)
     e[ax] = 1.0
     w = e - u[ax] * u
