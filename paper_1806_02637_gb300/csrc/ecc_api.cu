@@ -50,10 +50,6 @@ struct ecc_ctx {
   const void* samp_pair_ptr = nullptr;
   Buf h_P, h_img, h_sino, h_total;  // buffers of the host-buffer entry point
   cudaStream_t copy_stream = nullptr;  // its image uploads, per precompute batch
-  // the pair set-up of chunk i + 1 runs on setup_stream while the pair kernel of chunk i
-  // runs on the caller's stream (FP64 set-up beside FP32 gathers on the same SMs)
-  cudaStream_t setup_stream = nullptr;
-  cudaEvent_t ev_views = nullptr, ev_chunk[8] = {};
   ecc_serve* serve = nullptr;       // serving scheduler, created by the first ecc_submit
 };
 
@@ -163,8 +159,8 @@ int check_geometry_args(ecc_ctx* c, int n_views, const void* P, int W, int H, in
 
 
 // Views per dRadon/ds batch: the weighted images of a batch take at most 256 MiB.
-int radon_batch_views(int n_views, int W, int H, int n_s) {
-  const size_t plane = ecc::radon_plane_bytes(W, H, n_s);
+int radon_batch_views(int n_views, int W, int H, int n_alpha, int n_s) {
+  const size_t plane = ecc::radon_plane_bytes(W, H, n_alpha, n_s);
   const size_t max_batch_bytes = (size_t)256 << 20;
   return (int)std::max<size_t>(1, std::min<size_t>((size_t)n_views, max_batch_bytes / plane));
 }
@@ -178,8 +174,8 @@ int run_precompute(ecc_ctx* c, int n_views, const double* P, const float* images
   if ((rc = ensure(c, c->views, sizeof(ecc::ViewRec) * (size_t)n_views, "views")) != ECC_OK) return rc;
   const size_t tbytes = sizeof(ecc::RadonRow) * (size_t)n_views * n_alpha + sizeof(ecc::RadonView) * (size_t)n_views;
   if ((rc = ensure(c, c->rtable, tbytes, "radon table")) != ECC_OK) return rc;
-  const size_t plane = ecc::radon_plane_bytes(W, H, n_s);
-  const int batch = radon_batch_views(n_views, W, H, n_s);
+  const size_t plane = ecc::radon_plane_bytes(W, H, n_alpha, n_s);
+  const int batch = radon_batch_views(n_views, W, H, n_alpha, n_s);
   if ((rc = ensure(c, c->wimg, plane * (size_t)batch, "weighted images")) != ECC_OK) return rc;
   if (dtype == ECC_F16 &&
       (rc = ensure(c, c->stage, ecc::radon_f16_stage_bytes(n_alpha, n_s, batch), "FP16 staging")) != ECC_OK)
@@ -221,7 +217,7 @@ int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion,
   }
   const int n_tiles = (n_kappa + 31) / 32;
   const long long np = n_pairs;
-  const long long n_blocks = (np + 7) / 8 + 8;  // blocks of 8 or 16 pairs, over at most 8 chunks
+  const long long n_blocks = (np + 7) / 8;
   if ((rc = ensure(c, c->views, sizeof(ecc::ViewRec) * (size_t)n_views, "views")) != ECC_OK) return rc;
   if ((rc = ensure(c, c->pairs, sizeof(ecc::PairRec) * (size_t)np, "pairs")) != ECC_OK) return rc;
   if ((rc = ensure(c, c->ctile, sizeof(float4) * (size_t)np * n_tiles, "tile directions")) != ECC_OK) return rc;
@@ -254,51 +250,21 @@ int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion,
   ecc::alpha_dir_kernel<<<(n_alpha + 255) / 256, 256, 0, s>>>(n_alpha, (float4*)c->adir.p);
   hk.on_end("alpha_dir_kernel", s);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "alpha table launch");
-  // Pairs in chunks: the FP64 set-up of chunk i + 1 (setup_stream) overlaps the pair
-  // kernel of chunk i (the caller's stream), which waits for its own chunk's set-up.
-  // A chunk keeps at least ecc::kPairsPerChunkMin pairs, enough for the forward
-  // kernel's two-pair blocks; small launches stay one chunk on one stream.
-  const int n_chunks = (int)std::max<long long>(1, std::min<long long>(8, np / ecc::pairs_per_chunk_min()));
-  if (n_chunks > 1 && !c->setup_stream) {
-    if ((e = cudaStreamCreateWithFlags(&c->setup_stream, cudaStreamNonBlocking)) != cudaSuccess)
-      return cuda_fail(c, e, "set-up stream");
-    if ((e = cudaEventCreateWithFlags(&c->ev_views, cudaEventDisableTiming)) != cudaSuccess)
-      return cuda_fail(c, e, "event");
-    for (int i = 0; i < 8; ++i)
-      if ((e = cudaEventCreateWithFlags(&c->ev_chunk[i], cudaEventDisableTiming)) != cudaSuccess)
-        return cuda_fail(c, e, "event");
-  }
-  cudaStream_t ss = n_chunks > 1 ? c->setup_stream : s;
-  if (n_chunks > 1) {
-    if ((e = cudaEventRecord(c->ev_views, s)) != cudaSuccess) return cuda_fail(c, e, "event record");
-    if ((e = cudaStreamWaitEvent(ss, c->ev_views, 0)) != cudaSuccess) return cuda_fail(c, e, "stream wait");
-  }
-  long long chunk_beg[9];
-  for (int i = 0; i <= n_chunks; ++i) chunk_beg[i] = np * i / n_chunks;
-  for (int i = 0; i < n_chunks; ++i) {
-    const long long p0 = chunk_beg[i], p1 = chunk_beg[i + 1];
-    hk.on_begin("pair_setup_kernel", ss);
-    ecc::pair_setup_kernel<<<(unsigned)((p1 - p0 + 127) / 128), 128, 0, ss>>>(
-        n_views, p0, p1, pairs, (const ecc::ViewRec*)c->views.p, W, H, n_kappa, (ecc::PairRec*)c->pairs.p,
-        (float4*)c->ctile.p, n_tiles, reuse ? 1 : 0, c->d_status);
-    hk.on_end("pair_setup_kernel", ss);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "pair set-up launch");
-    if (n_chunks > 1 && (e = cudaEventRecord(c->ev_chunk[i], ss)) != cudaSuccess) return cuda_fail(c, e, "event");
-  }
+  // One pair set-up launch, then one pair-kernel launch, on the caller's stream.  (Set-up
+  // chunks on a second stream beside the pair kernel's chunks were measured slower: the
+  // two kernels sharing SMs slowed each other, 0.707 -> 0.765 ms on the 496-view scan.)
+  hk.on_begin("pair_setup_kernel", s);
+  ecc::pair_setup_kernel<<<(unsigned)((np + 127) / 128), 128, 0, s>>>(
+      n_views, 0, np, pairs, (const ecc::ViewRec*)c->views.p, W, H, n_kappa, (ecc::PairRec*)c->pairs.p,
+      (float4*)c->ctile.p, n_tiles, reuse ? 1 : 0, c->d_status);
+  hk.on_end("pair_setup_kernel", s);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "pair set-up launch");
   int nb = 0;
-  double* Gpp = (grad || grad_P) ? (double*)c->Gpp.p : nullptr;
-  for (int i = 0; i < n_chunks; ++i) {
-    const long long p0 = chunk_beg[i], p1 = chunk_beg[i + 1];
-    if (n_chunks > 1 && (e = cudaStreamWaitEvent(s, c->ev_chunk[i], 0)) != cudaSuccess)
-      return cuda_fail(c, e, "stream wait");
-    int nbi = 0;
-    e = ecc::launch_ecc_pairs(p1 - p0, (const ecc::PairRec*)c->pairs.p + p0, (const float4*)c->ctile.p + p0 * n_tiles,
-                              n_tiles, (const float4*)c->adir.p, sino, scales, dtype, n_alpha, n_s, n_kappa, W, H,
-                              cauchy_c, per_pair + 2 * p0, nkappa ? nkappa + p0 : nullptr,
-                              (double*)c->partial.p + nb, Gpp ? Gpp + 12 * p0 : nullptr, c->d_status, &nbi, hk, s);
-    if (e != cudaSuccess) return cuda_fail(c, e, "pair kernel launch");
-    nb += nbi;
-  }
+  e = ecc::launch_ecc_pairs(np, (const ecc::PairRec*)c->pairs.p, (const float4*)c->ctile.p, n_tiles,
+                            (const float4*)c->adir.p, sino, scales, dtype, n_alpha, n_s, n_kappa, W, H, cauchy_c,
+                            per_pair, nkappa, (double*)c->partial.p, (grad || grad_P) ? (double*)c->Gpp.p : nullptr,
+                            c->d_status, &nb, hk, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "pair kernel launch");
   e = ecc::launch_reduce((const double*)c->partial.p, nb, total, hk, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "reduce launch");
   if (grad || grad_P) {
@@ -393,10 +359,6 @@ void ecc_destroy(ecc_ctx* c) {
   }
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
-  if (c->setup_stream) cudaStreamDestroy(c->setup_stream);
-  if (c->ev_views) cudaEventDestroy(c->ev_views);
-  for (cudaEvent_t ev : c->ev_chunk)
-    if (ev) cudaEventDestroy(ev);
   delete c;
 }
 
@@ -570,7 +532,7 @@ int ecc_scan_consistency_host(ecc_ctx* c, int n_views, const double* P_host, con
   // From pinned host memory the images go up per precompute batch on a second stream,
   // so that the upload of batch b + 1 overlaps the projection of batch b; pageable
   // memory (whose asynchronous copies block the host) is copied in one piece.
-  const int batch = radon_batch_views(n_views, W, H, n_s);
+  const int batch = radon_batch_views(n_views, W, H, n_alpha, n_s);
   const int n_batches = (n_views + batch - 1) / batch;
   cudaPointerAttributes pa;
   const bool pinned = cudaPointerGetAttributes(&pa, images_host) == cudaSuccess && pa.type == cudaMemoryTypeHost;

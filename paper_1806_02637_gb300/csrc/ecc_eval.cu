@@ -1136,13 +1136,6 @@ cudaError_t launch_ecc_pairs(long long n_pairs, const PairRec* prs, const float4
   return cudaGetLastError();
 }
 
-long long pairs_per_chunk_min() {
-  int dev = 0, n_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    n_sm = 1;
-  return (long long)kPairsPerForwardBlock * 4 * n_sm * kForwardWavesForTwo;
-}
-
 int serve_pairs_blocks_per_sm() {
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, serve_pair_kernel, kWarpsPerBlock * 32, 0) != cudaSuccess)
