@@ -159,8 +159,8 @@ int check_geometry_args(ecc_ctx* c, int n_views, const void* P, int W, int H, in
 
 
 // Views per dRadon/ds batch: the weighted images of a batch take at most 256 MiB.
-int radon_batch_views(int n_views, int W, int H, int n_alpha, int n_s) {
-  const size_t plane = ecc::radon_plane_bytes(W, H, n_alpha, n_s);
+int radon_batch_views(int n_views, int W, int H, int n_s) {
+  const size_t plane = ecc::radon_plane_bytes(W, H, n_s);
   const size_t max_batch_bytes = (size_t)256 << 20;
   return (int)std::max<size_t>(1, std::min<size_t>((size_t)n_views, max_batch_bytes / plane));
 }
@@ -174,8 +174,8 @@ int run_precompute(ecc_ctx* c, int n_views, const double* P, const float* images
   if ((rc = ensure(c, c->views, sizeof(ecc::ViewRec) * (size_t)n_views, "views")) != ECC_OK) return rc;
   const size_t tbytes = sizeof(ecc::RadonRow) * (size_t)n_views * n_alpha + sizeof(ecc::RadonView) * (size_t)n_views;
   if ((rc = ensure(c, c->rtable, tbytes, "radon table")) != ECC_OK) return rc;
-  const size_t plane = ecc::radon_plane_bytes(W, H, n_alpha, n_s);
-  const int batch = radon_batch_views(n_views, W, H, n_alpha, n_s);
+  const size_t plane = ecc::radon_plane_bytes(W, H, n_s);
+  const int batch = radon_batch_views(n_views, W, H, n_s);
   if ((rc = ensure(c, c->wimg, plane * (size_t)batch, "weighted images")) != ECC_OK) return rc;
   if (dtype == ECC_F16 &&
       (rc = ensure(c, c->stage, ecc::radon_f16_stage_bytes(n_alpha, n_s, batch), "FP16 staging")) != ECC_OK)
@@ -532,7 +532,7 @@ int ecc_scan_consistency_host(ecc_ctx* c, int n_views, const double* P_host, con
   // From pinned host memory the images go up per precompute batch on a second stream,
   // so that the upload of batch b + 1 overlaps the projection of batch b; pageable
   // memory (whose asynchronous copies block the host) is copied in one piece.
-  const int batch = radon_batch_views(n_views, W, H, n_alpha, n_s);
+  const int batch = radon_batch_views(n_views, W, H, n_s);
   const int n_batches = (n_views + batch - 1) / batch;
   cudaPointerAttributes pa;
   const bool pinned = cudaPointerGetAttributes(&pa, images_host) == cudaSuccess && pa.type == cudaMemoryTypeHost;

@@ -94,9 +94,9 @@ cudaError_t launch_radon(const ViewRec* views, int n_views, const float* images,
                          int batch_views, const LaunchHooks& hooks, cudaStream_t stream,
                          const cudaEvent_t* batch_ready = nullptr);  // per batch: wait before reading its images
 size_t radon_f16_stage_bytes(int n_alpha, int n_s, int batch_views);
-int radon_pad(int W, int H, int n_alpha, int n_s);
+int radon_pad(int W, int H, int n_s);
 // Bytes of one view's weighted-image planes (interpolation pairs, both orientations).
-size_t radon_plane_bytes(int W, int H, int n_alpha, int n_s);
+size_t radon_plane_bytes(int W, int H, int n_s);
 
 cudaError_t launch_ecc_pairs(long long n_pairs, const PairRec* prs, const float4* ctile, int n_tiles,
                              const float4* alpha_dir, const void* sino, const float* scales, int dtype,

@@ -254,173 +254,6 @@ __global__ void __launch_bounds__(32 * kAlphaPerBlock) joseph_kernel(const Radon
   }
 }
 
-// ------------------------------------------------ Joseph line sums, alpha-major warps
-//
-// The same sums as joseph_kernel with another assignment of lines to lanes.  A warp
-// takes 8 consecutive alpha rows of one stepping mode and 15 consecutive outputs: lane
-// (ia, is) = (lane / 4, lane % 4) follows, at alpha row m0 + ia, the four half-step
-// lines k0 + 4 r + is (r = 0..3), i.e. the 16 lines k0 .. k0 + 15 of its row.  At one
-// image row the 32 lanes of a load then sit at 8 alpha rows x 4 neighbouring lines:
-// the lines of neighbouring alpha rows nearly coincide near the detector centre, so a
-// warp's 8-byte loads touch fewer 128-byte lines than 32 neighbouring lines of one
-// alpha row do (31 STEP apart).  The block's 8 warps take consecutive output chunks
-// of the same 8 alpha rows (adjacent image bands).  Positions, taps, 8-row partial sums
-// and the Kahan-compensated half-step differences are those of joseph_kernel; the
-// difference partner of line k0 + 4 r + 3 is lane (ia, 0) at step r + 1.
-constexpr int kAmAlpha = 8;                     // alpha rows per warp
-constexpr int kAmLanesS = 4;                    // lanes per alpha row
-constexpr int kAmSteps = 4;                     // lines per lane
-constexpr int kAmOut = kAmLanesS * kAmSteps - 1;  // 15 outputs per alpha row per warp
-constexpr int kAmWarps = 8;                     // warps per block (consecutive output chunks)
-
-// Alpha groups of the grid: each stepping mode's rows form a segment, cut into groups
-// of kAmAlpha (the last group of a segment may be short).
-struct AmSegments {
-  int start[4];  // segment starts (start[3] = n_alpha)
-  int groups[3];  // groups per segment
-};
-
-template <bool FULL>
-__device__ __forceinline__ void joseph_am_block(const float2* __restrict__ (&rp)[kAmSteps], const float (&f0)[kAmSteps],
-                                                float dyf, const float (&Mu)[kRowsPerAnchor], int ub, int is,
-                                                float (&acc)[kAmSteps], float (&comp)[kAmSteps]) {
-#pragma unroll
-  for (int i = 0; i < kRowsPerAnchor / kRowsPerBlock; ++i) {
-    float s[kAmSteps];
-#pragma unroll
-    for (int r = 0; r < kAmSteps; ++r) s[r] = 0.0f;
-#pragma unroll
-    for (int uu = 0; uu < kRowsPerBlock; ++uu) {
-      const int u = i * kRowsPerBlock + uu;
-      if (FULL || u < ub) {
-#pragma unroll
-        for (int r = 0; r < kAmSteps; ++r) {
-          const float xf = fmaf((float)u, dyf, f0[r]);
-          const float t = __fadd_rd(xf, Mu[u]);
-          const float f = xf - (t - Mu[u]);
-          const float2 vd = __ldg(rp[r] + __float_as_uint(t));
-          s[r] += fmaf(f, vd.y, vd.x);
-        }
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < kAmSteps; ++r) {
-      const float dn = __shfl_down_sync(0xffffffffu, s[r], 1);  // line + 1 of the same step (is < 3)
-      float nb = dn;
-      if (r + 1 < kAmSteps) {
-        const float up = __shfl_up_sync(0xffffffffu, s[r + 1 < kAmSteps ? r + 1 : r], 3);  // lane (ia, 0), step r + 1
-        nb = is == 3 ? up : dn;
-      }
-      kahan_add(nb - s[r], acc[r], comp[r]);
-    }
-  }
-}
-
-__global__ void __launch_bounds__(32 * kAmWarps) joseph_am_kernel(const RadonRow* __restrict__ table,
-                                                                   const RadonView* __restrict__ rv,
-                                                                   const float2* __restrict__ wimg, JosephArgs g,
-                                                                   AmSegments seg, float* __restrict__ out_f32,
-                                                                   __nv_bfloat16* __restrict__ out_bf16) {
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  const int ia = lane >> 2, is = lane & 3;
-  const int v = blockIdx.z;
-  // alpha group -> rows [m0, mend) of one segment (block-uniform)
-  int gy = (int)blockIdx.y, sg = 0;
-  while (sg < 2 && gy >= seg.groups[sg]) gy -= seg.groups[sg++];
-  const int m0 = seg.start[sg] + kAmAlpha * gy, mend = seg.start[sg + 1];
-  const int m = m0 + ia;
-  const bool m_ok = m < mend;
-  const int mm = m_ok ? m : mend - 1;  // lanes past the segment repeat its last row (not stored)
-  const int k0 = ((int)blockIdx.x * kAmWarps + warp) * kAmOut;
-  if (k0 >= g.n_s) return;  // warp-uniform
-  const RadonRow row = table[(size_t)v * g.n_alpha + mm];
-  const bool rows = row.rows_mode != 0;  // uniform over the segment
-  const float2* img = wimg + (size_t)v * g.plane + (rows ? 0 : (size_t)g.H * g.pitch_r);
-  const int pitch = rows ? g.pitch_r : g.pitch_c;
-  const int n_steps = rows ? g.H : g.W;
-  const int limit = rows ? g.W : g.H;
-  const int kf = k0 + is;  // this lane's first line; its last is kf + 4 (kAmSteps - 1)
-  // image rows where this lane's lines are inside the interpolation support, then the
-  // union over the warp
-  int s_lo = 0, s_hi = n_steps;
-  {
-    const float scale = 1.0f / 65536.0f;
-    const float xa = (float)((row.B0 + (long long)kf * row.STEP) >> 16) * scale;
-    const float xb = (float)((row.B0 + (long long)(kf + kAmLanesS * (kAmSteps - 1)) * row.STEP) >> 16) * scale;
-    const float dy = (float)(row.DY >> 16) * scale;
-    const float mn = fminf(xa, xb) - 2.0f, mx = fmaxf(xa, xb) + 2.0f;
-    const float lo_t = -1.0f, hi_t = (float)limit;
-    if (fabsf(dy) > 1e-6f) {
-      const float s1 = (lo_t - mx) / dy, s2 = (hi_t - mn) / dy;
-      const float cap = (float)n_steps + 4.0f;
-      const float sl = fminf(fmaxf(fminf(s1, s2), -4.0f), cap);
-      const float sh = fminf(fmaxf(fmaxf(s1, s2), -4.0f), cap);
-      s_lo = max(0, (int)floorf(sl) - 1);
-      s_hi = min(n_steps, (int)ceilf(sh) + 2);
-    } else if (mx < lo_t || mn > hi_t) {
-      s_lo = n_steps;
-      s_hi = 0;
-    }
-    if (s_hi < s_lo) {  // empty: neutral for the reduction
-      s_lo = n_steps;
-      s_hi = 0;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      s_lo = min(s_lo, __shfl_xor_sync(0xffffffffu, s_lo, o));
-      s_hi = max(s_hi, __shfl_xor_sync(0xffffffffu, s_hi, o));
-    }
-    if (s_hi < s_lo) s_hi = s_lo;
-  }
-  const float dyf = (float)((double)row.DY * (1.0 / 4294967296.0));
-  const long long DY16 = (long long)kRowsPerAnchor * row.DY;
-  const long long STEP4 = (long long)kAmLanesS * row.STEP;
-  float Mu[kRowsPerAnchor];
-#pragma unroll
-  for (int u = 0; u < kRowsPerAnchor; ++u) Mu[u] = kMagic + (float)(u * pitch);
-  long long X = row.B0 + (long long)kf * row.STEP + (long long)s_lo * row.DY;
-  float acc[kAmSteps], comp[kAmSteps];
-#pragma unroll
-  for (int r = 0; r < kAmSteps; ++r) acc[r] = comp[r] = 0.0f;
-  const uint64_t img_b = reinterpret_cast<uint64_t>(img) - 8ull * kMagicBits;
-  for (int j0 = s_lo; j0 < s_hi; j0 += kRowsPerAnchor) {
-    const float2* rp[kAmSteps];
-    float f0[kAmSteps];
-#pragma unroll
-    for (int r = 0; r < kAmSteps; ++r) {
-      const long long Xr = X + (long long)r * STEP4;
-      const int xi0 = (int)(Xr >> 32);
-      f0[r] = __uint_as_float(0x3f800000u | ((unsigned)Xr >> 9)) - 1.0f;
-      rp[r] = reinterpret_cast<const float2*>(img_b + 8ull * (uint64_t)((long long)j0 * pitch + g.pad + xi0));
-    }
-    const int n = s_hi - j0;
-    if (n >= kRowsPerAnchor)
-      joseph_am_block<true>(rp, f0, dyf, Mu, n, is, acc, comp);
-    else
-      joseph_am_block<false>(rp, f0, dyf, Mu, n, is, acc, comp);
-    X += DY16;
-  }
-  if (!m_ok) return;
-  const RadonView r = rv[v];
-  const float rd = (row.inv_len / g.ds);
-#pragma unroll
-  for (int st = 0; st < kAmSteps; ++st) {
-    const int k = kf + kAmLanesS * st;
-    if ((st < kAmSteps - 1 || is < kAmLanesS - 1) && k < g.n_s) {
-      const float sn = ((float)k - 0.5f * (float)(g.n_s - 1)) * g.ds;
-      const float spp = sn - (r.u0 - 0.5f * (float)(g.W - 1)) * row.ca - (r.v0 - 0.5f * (float)(g.H - 1)) * row.sa;
-      const float wgt = (r.D * r.D + spp * spp) / (r.D * r.D);
-      const float val = (acc[st] - comp[st]) * rd * wgt;
-      const size_t o = ((size_t)v * g.n_alpha + m) * g.n_s + k;
-      if (out_bf16)
-        out_bf16[o] = __float2bfloat16_rn(val);
-      else
-        out_f32[o] = val;
-    }
-  }
-}
-
 // FP16 storage: per-view scale = max|S| / 2^14 (1 if the view is all zero), so
 // every stored value is in FP16's normal range; stored = S / scale.  The max of a view
 // is split over gridDim.x blocks, each folding its part into the view's slot by an
@@ -452,44 +285,16 @@ __global__ void quantize_f16_kernel(const float* __restrict__ s32, size_t per_vi
 
 }  // namespace
 
-namespace {
-
-// Zero margin the alpha-major kernel needs: the widest spread of its lanes along the
-// interpolation axis at one image row, 7 alpha rows (|dx/dalpha| = |s sin a - y'| /
-// cos^2 a, |s| up to half the diagonal plus 15 lines, |y'| up to half the image, cos^2 a
-// >= 1/2 in its mode) plus 15 lines (STEP <= ds sqrt 2), plus the row-range margins.
-int am_pad(int W, int H, int n_alpha, int n_s) {
-  const double diag = sqrt((double)W * W + (double)H * H);
-  const double ds = diag / (n_s - 1);
-  const double dalpha = 3.14159265358979323846 / n_alpha;
-  const double alpha_spread = (kAmAlpha - 1) * dalpha * ((diag + 30.0 * ds) / 1.41421356237309515 + (double)max(W, H));
-  const double s_spread = kAmOut * ds * 1.41421356237309515;
-  return (int)ceil(alpha_spread + s_spread + 8.0);
-}
-
-// span of 32 neighbouring lines along the interpolation axis (|cos| or |sin| >=
-// 1/sqrt 2 in their mode) plus the margins of the per-warp row range
-int s_major_pad(int W, int H, int n_s) {
+int radon_pad(int W, int H, int n_s) {
+  // span of 32 neighbouring lines along the interpolation axis (|cos| or |sin| >=
+  // 1/sqrt 2 in their mode) plus the margins of the per-warp row range
   const double ds = sqrt((double)W * W + (double)H * H) / (n_s - 1);
-  return (int)ceil(31.0 * ds * 1.41421356237309515 + 8.0);
-}
-
-}  // namespace
-
-// Zero margin of the weighted-image planes for the kernel launch_radon uses: the
-// alpha-major kernel where its margin fits, else joseph_kernel (its clamped variant,
-// margin 2, for grids so coarse that even its margin would not fit).
-int radon_pad(int W, int H, int n_alpha, int n_s) {
-  const int am = am_pad(W, H, n_alpha, n_s);
-  if (am <= kMaxPad) return am;
-  const int need = s_major_pad(W, H, n_s);
+  const int need = (int)ceil(31.0 * ds * 1.41421356237309515 + 8.0);
   return need <= kMaxPad ? need : 2;  // 2: clamped variant
 }
 
-bool radon_alpha_major(int W, int H, int n_alpha, int n_s) { return am_pad(W, H, n_alpha, n_s) <= kMaxPad; }
-
-size_t radon_plane_bytes(int W, int H, int n_alpha, int n_s) {
-  const int pad = radon_pad(W, H, n_alpha, n_s);
+size_t radon_plane_bytes(int W, int H, int n_s) {
+  const int pad = radon_pad(W, H, n_s);
   return sizeof(float2) * ((size_t)H * (W + 2 * pad) + (size_t)W * (H + 2 * pad));
 }
 
@@ -517,26 +322,13 @@ cudaError_t launch_radon(const ViewRec* views, int n_views, const float* images,
   jg.H = H;
   jg.n_alpha = n_alpha;
   jg.n_s = n_s;
-  jg.pad = radon_pad(W, H, n_alpha, n_s);
-  const bool alpha_major = radon_alpha_major(W, H, n_alpha, n_s);
+  jg.pad = radon_pad(W, H, n_s);
   const bool clamp = jg.pad == 2;
   jg.pitch_r = W + 2 * jg.pad;
   jg.pitch_c = H + 2 * jg.pad;
-  jg.plane = radon_plane_bytes(W, H, n_alpha, n_s) / sizeof(float2);
+  jg.plane = radon_plane_bytes(W, H, n_s) / sizeof(float2);
   jg.ds = (float)(sqrt((double)W * W + (double)H * H) / (n_s - 1));
   const int n_chunks = (n_s + 30) / 31;
-  // alpha-major grid: stepping-mode segments of rows in groups of kAmAlpha
-  AmSegments seg;
-  seg.start[0] = 0;
-  seg.start[1] = n_alpha / 4 + 1;           // rows mode: 4 m <= n_alpha
-  seg.start[2] = (3 * n_alpha + 3) / 4;     // rows mode again: 4 m >= 3 n_alpha
-  seg.start[3] = n_alpha;
-  int am_groups = 0;
-  for (int i = 0; i < 3; ++i) {
-    seg.groups[i] = (max(seg.start[i + 1] - seg.start[i], 0) + kAmAlpha - 1) / kAmAlpha;
-    am_groups += seg.groups[i];
-  }
-  const int am_chunks = (n_s + kAmOut * kAmWarps - 1) / (kAmOut * kAmWarps);
   float2* wv = reinterpret_cast<float2*>(wimg);
   for (int v0 = 0; v0 < n_views; v0 += batch_views) {
     const int nb = min(batch_views, n_views - v0);
@@ -556,16 +348,12 @@ cudaError_t launch_radon(const ViewRec* views, int n_views, const float* images,
     const size_t oo = (size_t)v0 * n_alpha * n_s;
     float* of = dtype == 0 ? (float*)sino_out + oo : (dtype == 1 ? stage : nullptr);
     __nv_bfloat16* ob = dtype == 2 ? (__nv_bfloat16*)sino_out + oo : nullptr;
+    const dim3 grid(n_chunks, (n_alpha + kAlphaPerBlock - 1) / kAlphaPerBlock, nb), block(32 * kAlphaPerBlock);
     hooks.on_begin("joseph_kernel", stream);
-    if (alpha_major) {
-      joseph_am_kernel<<<dim3(am_chunks, am_groups, nb), 32 * kAmWarps, 0, stream>>>(tb, rv + v0, wv, jg, seg, of, ob);
-    } else {
-      const dim3 grid(n_chunks, (n_alpha + kAlphaPerBlock - 1) / kAlphaPerBlock, nb), block(32 * kAlphaPerBlock);
-      if (clamp)
-        joseph_kernel<true><<<grid, block, 0, stream>>>(tb, rv + v0, wv, jg, of, ob);
-      else
-        joseph_kernel<false><<<grid, block, 0, stream>>>(tb, rv + v0, wv, jg, of, ob);
-    }
+    if (clamp)
+      joseph_kernel<true><<<grid, block, 0, stream>>>(tb, rv + v0, wv, jg, of, ob);
+    else
+      joseph_kernel<false><<<grid, block, 0, stream>>>(tb, rv + v0, wv, jg, of, ob);
     hooks.on_end("joseph_kernel", stream);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -93,7 +93,7 @@ Layout layout_of(const ecc_job& j) {
   o = 0;
   L.images = take(n * (size_t)j.W * j.H * sizeof(float));
   L.rtable = take(n * (size_t)j.n_alpha * sizeof(ecc::RadonRow) + n * sizeof(ecc::RadonView));
-  const size_t plane = ecc::radon_plane_bytes(j.W, j.H, j.n_alpha, j.n_s);
+  const size_t plane = ecc::radon_plane_bytes(j.W, j.H, j.n_s);
   L.batch = (int)std::max<size_t>(1, std::min<size_t>(n, ((size_t)256 << 20) / plane));
   L.wimg = take(plane * (size_t)L.batch);
   L.stage = take(j.dtype == ECC_F16 ? ecc::radon_f16_stage_bytes(j.n_alpha, j.n_s, L.batch) : 0);
