@@ -437,15 +437,19 @@ __device__ __forceinline__ void series_position(const float4* __restrict__ rec, 
   for (int k = NT - 2; k >= 1; --k) sr = fmaf(sr, q.t, c[kSer + k]);
   sr = fmaf(c[kSer], q.tmd, q.t2 * sr);
   const float lin = h1.y * q.jj;  // gh * jj: exact
-  const float Li = floorf(lin);
+  // floors and integer parts by one round-down add against M = 1.5 * 2^23 (float spacing
+  // 1 in [2^23, 2^24)): RD(x + M) = M + floor(x) exactly for |x| < 2^22, and its bit
+  // pattern minus that of M is floor(x) as an integer (no conversion instructions).
+  // Masked lanes may carry larger values: their rows are rejected by the vote below.
+  const float M = 12582912.0f;
+  const float tl = __fadd_rd(lin, M);
   const float fa_ = h0.z + da;
-  const float fs_ = (h0.w + (lin - Li)) + fmaf(h1.z, q.jj, sr);
-  const float mf = floorf(fa_), nf = floorf(fs_);
-  // unsigned sums: a masked lane may carry any value; its row is rejected below
-  mu = (unsigned)__float_as_int(h0.x) + (unsigned)(int)mf;
-  n = (int)((unsigned)__float_as_int(h0.y) + (unsigned)(int)(Li + nf));
-  fa = fa_ - mf;
-  fs = fs_ - nf;
+  const float fs_ = (h0.w + (lin - (tl - M))) + fmaf(h1.z, q.jj, sr);
+  const float ta = __fadd_rd(fa_, M), tn = __fadd_rd(fs_, M);
+  mu = (unsigned)__float_as_int(h0.x) + (__float_as_uint(ta) - 0x4B400000u);
+  n = (int)((unsigned)__float_as_int(h0.y) + (__float_as_uint(tl) - 0x4B400000u) + (__float_as_uint(tn) - 0x4B400000u));
+  fa = fa_ - (ta - M);
+  fs = fs_ - (tn - M);
 }
 
 // Bilinear value at row m (0 <= m <= n_alpha - 2) and bin n (clamped to [0, n_s - 2]);
@@ -765,6 +769,17 @@ __device__ __forceinline__ float sample_grad_rows(const T* __restrict__ sv, int 
   return scale * sign * fmaf(fa, v1 - v0, v0);
 }
 
+// The lane's line l = A c_k of one view from its tile's record (written by the anchor
+// pass): c_k = cos(delta) c_t + sin(delta) c_t_perp, so l = cos(delta) (A c_t) + sin(delta)
+// (A c_t_perp), with A c_t = (x.x, x.y, x.z) and A c_t_perp = (x.w, y.x, y.y).
+__device__ __forceinline__ void tile_line(const float4* __restrict__ lp, float cd, float sd, float& l0, float& l1,
+                                          float& l2) {
+  const float4 x = lp[0], y = lp[1];
+  l0 = fmaf(sd, x.w, cd * x.x);
+  l1 = fmaf(sd, y.x, cd * x.y);
+  l2 = fmaf(sd, y.y, cd * x.z);
+}
+
 // S_a - S_b of this lane's sample and the line gradients of both views, by the general
 // per-sample code.
 template <typename T>
@@ -772,8 +787,10 @@ __device__ __forceinline__ float tile_adjoint_general_body(const float4* __restr
                                                           const float4* __restrict__ rb, const LaneGeom& q,
                                                           const T* __restrict__ sa, const T* __restrict__ sb,
                                                           float sca, float scb, int n_alpha, int n_s,
-                                                          float inv_dalpha, float inv_ds_f, const float (&Af)[12],
-                                                          float ckx, float cky, float (&ga)[3], float (&gb)[3]) {
+                                                          float inv_dalpha, float inv_ds_f,
+                                                          const float4* __restrict__ lpa,
+                                                          const float4* __restrict__ lpb, float (&ga)[3],
+                                                          float (&gb)[3]) {
   Loc la, lb;
   {
     const Anchor an = load_anchor(ra);
@@ -785,10 +802,11 @@ __device__ __forceinline__ float tile_adjoint_general_body(const float4* __restr
     lb = an.ser != 0.0f ? locate_series(an, q.t, q.tmd, q.jj, n_alpha, n_s)
                         : locate(an, q.cd, q.sd, q.jj, q.de, n_alpha, n_s, inv_dalpha, inv_ds_f);
   }
-  const float Sa = sample_grad(sa, n_alpha, n_s, la, inv_dalpha, inv_ds_f, Af[0] * ckx + Af[1] * cky,
-                               Af[2] * ckx + Af[3] * cky, Af[4] * ckx + Af[5] * cky, sca, ga);
-  const float Sb = sample_grad(sb, n_alpha, n_s, lb, inv_dalpha, inv_ds_f, Af[6] * ckx + Af[7] * cky,
-                               Af[8] * ckx + Af[9] * cky, Af[10] * ckx + Af[11] * cky, scb, gb);
+  float l0, l1, l2;
+  tile_line(lpa, q.cd, q.sd, l0, l1, l2);
+  const float Sa = sample_grad(sa, n_alpha, n_s, la, inv_dalpha, inv_ds_f, l0, l1, l2, sca, ga);
+  tile_line(lpb, q.cd, q.sd, l0, l1, l2);
+  const float Sb = sample_grad(sb, n_alpha, n_s, lb, inv_dalpha, inv_ds_f, l0, l1, l2, scb, gb);
   return Sa - Sb;
 }
 
@@ -797,10 +815,10 @@ __device__ __noinline__ float tile_adjoint_general(const float4* __restrict__ ra
                                                   const LaneGeom& q, const T* __restrict__ sa,
                                                   const T* __restrict__ sb, float sca, float scb, int n_alpha,
                                                   int n_s, float inv_dalpha, float inv_ds_f,
-                                                  const float (&Af)[12], float ckx, float cky, float (&ga)[3],
-                                                  float (&gb)[3]) {
-  return tile_adjoint_general_body<T>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f, Af, ckx, cky,
-                                      ga, gb);
+                                                  const float4* __restrict__ lpa, const float4* __restrict__ lpb,
+                                                  float (&ga)[3], float (&gb)[3]) {
+  return tile_adjoint_general_body<T>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f, lpa, lpb, ga,
+                                      gb);
 }
 
 template <typename T, int NT>
@@ -808,8 +826,8 @@ __device__ __forceinline__ float tile_adjoint_series(const float4* __restrict__ 
                                                     const LaneGeom& q, const T* __restrict__ sa,
                                                     const T* __restrict__ sb, float sca, float scb, int n_alpha,
                                                     int n_s, float inv_dalpha, float inv_ds_f,
-                                                    const float (&Af)[12], float ckx, float cky, float (&ga)[3],
-                                                    float (&gb)[3]) {
+                                                    const float4* __restrict__ lpa,
+                                                    const float4* __restrict__ lpb, float (&ga)[3], float (&gb)[3]) {
   unsigned ma, mb;
   int na, nb;
   float faa, fsa, fab, fsb;
@@ -817,14 +835,13 @@ __device__ __forceinline__ float tile_adjoint_series(const float4* __restrict__ 
   series_position<NT>(rb, q, mb, nb, fab, fsb);
   const unsigned last = (unsigned)(n_alpha - 1);
   if (__any_sync(0xffffffffu, ma >= last || mb >= last))
-    return tile_adjoint_general<T>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f, Af, ckx, cky,
-                                   ga, gb);
-  const float Sa = sample_grad_rows(sa, n_s, ma, na, faa, fsa, ra[1].x, inv_dalpha, inv_ds_f,
-                                    Af[0] * ckx + Af[1] * cky, Af[2] * ckx + Af[3] * cky, Af[4] * ckx + Af[5] * cky,
-                                    sca, ga);
-  const float Sb = sample_grad_rows(sb, n_s, mb, nb, fab, fsb, rb[1].x, inv_dalpha, inv_ds_f,
-                                    Af[6] * ckx + Af[7] * cky, Af[8] * ckx + Af[9] * cky,
-                                    Af[10] * ckx + Af[11] * cky, scb, gb);
+    return tile_adjoint_general<T>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f, lpa, lpb, ga,
+                                   gb);
+  float l0, l1, l2;
+  tile_line(lpa, q.cd, q.sd, l0, l1, l2);
+  const float Sa = sample_grad_rows(sa, n_s, ma, na, faa, fsa, ra[1].x, inv_dalpha, inv_ds_f, l0, l1, l2, sca, ga);
+  tile_line(lpb, q.cd, q.sd, l0, l1, l2);
+  const float Sb = sample_grad_rows(sb, n_s, mb, nb, fab, fsb, rb[1].x, inv_dalpha, inv_ds_f, l0, l1, l2, scb, gb);
   return Sa - Sb;
 }
 
@@ -832,15 +849,14 @@ template <typename T>
 __device__ __forceinline__ float tile_adjoint(const float4* __restrict__ ra, const float4* __restrict__ rb,
                                              const LaneGeom& q, const T* __restrict__ sa, const T* __restrict__ sb,
                                              float sca, float scb, int n_alpha, int n_s, float inv_dalpha,
-                                             float inv_ds_f, const float (&Af)[12], float ckx, float cky,
-                                             float (&ga)[3], float (&gb)[3]) {
+                                             float inv_ds_f, const float4* __restrict__ lpa,
+                                             const float4* __restrict__ lpb, float (&ga)[3], float (&gb)[3]) {
   const float na = ra[1].w, nb = rb[1].w;
   if (na == 0.0f || nb == 0.0f)
-    return tile_adjoint_general<T>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f, Af, ckx, cky,
-                                   ga, gb);
+    return tile_adjoint_general<T>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f, lpa, lpb, ga, gb);
   const float nt = fmaxf(na, nb);
 #define ECC_ADJ(NT_) \
-  return tile_adjoint_series<T, NT_>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f, Af, ckx, cky, ga, gb)
+  return tile_adjoint_series<T, NT_>(ra, rb, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f, lpa, lpb, ga, gb)
   if (nt <= 3.0f) ECC_ADJ(3);
   if (nt <= 4.0f) ECC_ADJ(4);
   if (nt <= 6.0f) ECC_ADJ(6);
@@ -858,7 +874,7 @@ __device__ __forceinline__ float tile_adjoint(const float4* __restrict__ ra, con
 // and formulas, so the same values).
 template <typename T, bool FAST>
 __device__ __forceinline__ double pair_warp_adjoint(const PairArgs& g, long long p, int lane,
-                                                    float4* __restrict__ recw) {
+                                                    float4* __restrict__ recw, float4* __restrict__ lpw) {
   const PairRec& pr = g.prs[p];
   const int nk_in = pr.status == 0 ? pr.nk : 0;
   const int n_tiles = g.n_tiles, n_alpha = g.n_alpha, n_s = g.n_s, K = g.K;
@@ -895,9 +911,6 @@ __device__ __forceinline__ double pair_warp_adjoint(const PairArgs& g, long long
     const int r0lo = pr.r0lo, r1lo = pr.r1lo;
     const unsigned len0 = (unsigned)max(pr.r0hi - pr.r0lo, 0), len1 = (unsigned)max(pr.r1hi - pr.r1lo, 0);
     const float4* __restrict__ ct = g.ctile + p * n_tiles;
-    float Af[12];
-#pragma unroll
-    for (int i = 0; i < 12; ++i) Af[i] = (&pr.Af[0][0])[2 * i];
     auto one_tile = [&](int t, const LaneGeom& q, bool valid) {
       const float4 ctd = ct[t];
       const float ckx = ctd.x * q.cd - ctd.y * q.sd, cky = ctd.x * q.sd + ctd.y * q.cd;
@@ -905,9 +918,9 @@ __device__ __forceinline__ double pair_warp_adjoint(const PairArgs& g, long long
       const int tt = t & 15;
       const float dd =
           FAST ? tile_adjoint<T>(recw + kRec * tt, recw + kRec * (16 + tt), q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha,
-                                 inv_ds_f, Af, ckx, cky, ga, gb)
+                                 inv_ds_f, lpw + 2 * tt, lpw + 2 * (16 + tt), ga, gb)
                : tile_adjoint_general_body<T>(recw + kRec * tt, recw + kRec * (16 + tt), q, sa, sb, sca, scb, n_alpha,
-                                              n_s, inv_dalpha, inv_ds_f, Af, ckx, cky, ga, gb);
+                                              n_s, inv_dalpha, inv_ds_f, lpw + 2 * tt, lpw + 2 * (16 + tt), ga, gb);
       acc += valid ? dd * dd : 0.0f;
       // masked samples may sit anywhere (their slopes need not be finite): skipped, not
       // multiplied by zero
@@ -927,8 +940,19 @@ __device__ __forceinline__ double pair_warp_adjoint(const PairArgs& g, long long
         const int v = lane >> 4;
         int t = t0 + (lane & 15);
         if (t >= n_tiles) t = n_tiles - 1;
-        store_anchor(recw + kRec * lane, make_anchor(pr.Af[v], ct[t], g.alpha_dir, n_alpha, inv_dalpha, inv_ds,
+        const float4 c = ct[t];
+        store_anchor(recw + kRec * lane, make_anchor(pr.Af[v], c, g.alpha_dir, n_alpha, inv_dalpha, inv_ds,
                                                   half_ns1, inv_ds_f, dk, tan_half_tile, kGhMask32, kSerLimit32, 10));
+        // the tile's lines A c_t and A c_t_perp (FP32) for the per-sample line gradients
+        const float* A = pr.Af[v];  // (hi, lo) pairs: A[4 i] = row i, column 0; A[4 i + 2] = column 1
+        float lc[3], pc[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          lc[i] = fmaf(A[4 * i + 2], c.y, A[4 * i] * c.x);
+          pc[i] = fmaf(A[4 * i + 2], c.x, -A[4 * i] * c.y);
+        }
+        lpw[2 * lane] = make_float4(lc[0], lc[1], lc[2], pc[0]);
+        lpw[2 * lane + 1] = make_float4(pc[1], pc[2], 0.0f, 0.0f);
       }
       __syncwarp();
       const int tmax = min(16, n_tiles - t0);
@@ -978,13 +1002,14 @@ __device__ __forceinline__ double pair_warp_adjoint(const PairArgs& g, long long
 // One block of consecutive pairs (kWarpsPerBlock for the adjoint, two per warp for the
 // forward kernel): their e summed in a fixed order into partial[blk].
 template <typename T, bool GRAD, bool SERVE = false>
-__device__ __forceinline__ void pair_block(const PairArgs& g, long long blk, double* e_warp, float4* recs) {
+__device__ __forceinline__ void pair_block(const PairArgs& g, long long blk, double* e_warp, float4* recs,
+                                           float4* lps) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   float4* recw = recs + (size_t)wib * 32 * kRec;
   double e_val = 0.0;
   if (GRAD) {
     const long long p = blk * kWarpsPerBlock + wib;
-    if (p < g.n_pairs) e_val = pair_warp_adjoint<T, !SERVE>(g, p, lane, recw);  // warp-uniform
+    if (p < g.n_pairs) e_val = pair_warp_adjoint<T, !SERVE>(g, p, lane, recw, lps + (size_t)wib * 64);  // warp-uniform
   } else {
     // two pairs per warp (blk 2W + w and blk 2W + W + w, W warps: the block's warps run
     // neighbouring pairs side by side) when the launch has fewer blocks than pairs / W
@@ -1008,8 +1033,9 @@ __device__ __forceinline__ void pair_block(const PairArgs& g, long long blk, dou
 template <typename T, bool GRAD>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, GRAD ? 3 : 4) ecc_pair_kernel(PairArgs g) {
   __shared__ double e_warp[kWarpsPerBlock];
-  __shared__ float4 recs[kWarpsPerBlock * 32 * kRec];  // anchor records, 5.5 KB per warp
-  pair_block<T, GRAD>(g, blockIdx.x, e_warp, recs);
+  __shared__ float4 recs[kWarpsPerBlock * 32 * kRec];         // anchor records, 5.5 KB per warp
+  __shared__ float4 lps[GRAD ? kWarpsPerBlock * 64 : 1];      // the adjoint's tile lines, 1 KB per warp
+  pair_block<T, GRAD>(g, blockIdx.x, e_warp, recs, lps);
 }
 
 // Fixed-order sum of n block partials by one block of 1024 threads: deterministic.
@@ -1044,6 +1070,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 3) serve_pair_kernel(cons
                                                                          unsigned long long* __restrict__ next) {
   __shared__ double e_warp[kWarpsPerBlock];
   __shared__ float4 recs[kWarpsPerBlock * 32 * kRec];  // anchor records, 5.5 KB per warp
+  __shared__ float4 lps[kWarpsPerBlock * 64];          // the adjoint's tile lines, 1 KB per warp
   __shared__ long long item;
   const long long total = boff[n_jobs];
   for (;;) {
@@ -1057,13 +1084,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 3) serve_pair_kernel(cons
     const long long blk = it - boff[j];
     switch (jobs[j].dtype) {  // block-uniform
       case 0:
-        pair_block<float, true, true>(g, blk, e_warp, recs);
+        pair_block<float, true, true>(g, blk, e_warp, recs, lps);
         break;
       case 1:
-        pair_block<__half, true, true>(g, blk, e_warp, recs);
+        pair_block<__half, true, true>(g, blk, e_warp, recs, lps);
         break;
       default:
-        pair_block<__nv_bfloat16, true, true>(g, blk, e_warp, recs);
+        pair_block<__nv_bfloat16, true, true>(g, blk, e_warp, recs, lps);
         break;
     }
   }
