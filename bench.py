@@ -477,7 +477,7 @@ def storage_forms(ctx, P, images, cfg, total_f32, reps=10, oracle=None, l2_gbs=N
     return out
 
 
-def l2_read_rate(dev, sizes_mb=(32, 64, 96), reps=200):
+def l2_read_rate(dev, sizes_mb=(32, 64, 96), reps=20):
     """Read rate of a buffer resident in L2 (129 MB), the denominator of the L2
     fractions: the library's diagnostic read kernel (16-byte loads that skip L1, 8
     blocks per SM), CUDA events around `reps` launches; the best of three sizes."""
@@ -493,16 +493,17 @@ def l2_read_rate(dev, sizes_mb=(32, 64, 96), reps=200):
             rates[f"{mb}MB"] = g.value
     best = max(rates.values()) if rates else float("nan")
     return {"gbs": best, "by_size_gbs": rates,
-            "how": f"L2-resident buffers read with ld.global.cg float4, 8 blocks per SM, {reps} launches, CUDA events"}
+            "how": f"L2-resident buffers read with ld.global.cg float4 (about 1 GB per launch), 8 blocks per SM, "
+                   f"{reps} launches, CUDA events"}
 
 
 # ------------------------------------------------------------------ precision leg (1240-view scan)
 def c4_leg(ctx, l2_gbs, reps=5):
     """The precision workload: 1240 views over 360 degrees, 976x976 detector (0.3 mm),
-    60 seeded ellipsoids, 1024 x 1382 dRadon/ds stored in FP16 and BF16, 1024 kappa, all
-    768,180 pairs.  Times the precompute and the evaluation (the library's CUDA events,
-    inputs resident), the pair kernel's algorithmic bytes (16 B per line pair) against
-    HBM and L2, and the oracle on 16 seeded views: their dRadon/ds and the 120 pairs
+    60 seeded ellipsoids, 1024 x 1382 dRadon/ds stored in FP16 and BF16 (and FP32 for
+    comparison), 1024 kappa, all 768,180 pairs.  Times the precompute and the evaluation
+    (the library's CUDA events, inputs resident), the pair kernel's algorithmic bytes (16 B
+    per line pair in FP16/BF16, 32 B in FP32) against HBM and L2, and the oracle on 16 seeded views: their dRadon/ds and the 120 pairs
     among them (timed, and extrapolated per view and per pair to the whole job), with
     those pairs' errors against the oracle and the stored sinograms' errors."""
     import torch
@@ -538,7 +539,8 @@ def c4_leg(ctx, l2_gbs, reps=5):
                             "sample": (f"dRadon/ds of 16 seeded views ({tb - ta:.2f} s) and the ECC of the 120 pairs "
                                        f"among them ({tc - tb:.3f} s), extrapolated per view and per pair to the "
                                        f"whole job ({job_s:.0f} s)")}}
-    for name, dt in (("float16", torch.float16), ("bfloat16", torch.bfloat16)):
+    for name, dt in (("float16", torch.float16), ("bfloat16", torch.bfloat16), ("float32", torch.float32)):
+        esize = 4 if dt == torch.float32 else 2
         S, scales = ecc.ecc_precompute_radon_derivative(ctx, P, images, cfg.n_alpha, cfg.n_s, dtype=dt)
         torch.cuda.synchronize()
         ecc.ecc_profile_read(ctx)
@@ -558,8 +560,8 @@ def c4_leg(ctx, l2_gbs, reps=5):
         ecc.ecc_profile_enable(ctx, False)
         eval_ms = wall_ms(lambda: ecc.ecc_evaluate(ctx, P, S, cfg.W, cfg.H, cfg.K, scales=scales, total=tot,
                                                    want_per_pair=False), reps)
-        pk_ms = prof["ecc_pair_kernel"][1] / reps   # all chunks of one evaluation
-        gbs = 16.0 * units / (pk_ms / 1e3) / 1e9
+        pk_ms = prof["ecc_pair_kernel"][1] / reps
+        gbs = 8.0 * esize * units / (pk_ms / 1e3) / 1e9
         r = ecc.ecc_evaluate(ctx, P, S, cfg.W, cfg.H, cfg.K, scales=scales)
         d = r["per_pair"][:, 0].cpu().numpy()
         stored = S[torch.as_tensor(views, device=dev)].float()
@@ -571,7 +573,8 @@ def c4_leg(ctx, l2_gbs, reps=5):
                      "line_pairs_per_s": units / (eval_ms / 1e3), "pair_kernel_ms": pk_ms,
                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks.get("hbm_gbs", 6800.0),
                                   "unit": "GB/s", "frac": gbs / peaks.get("hbm_gbs", 6800.0),
-                                  "frac_of_l2": gbs / l2_gbs, "work": "16 B (2 views x 4 taps x 2 B) per line pair"},
+                                  "frac_of_l2": gbs / l2_gbs,
+                                  "work": f"{8 * esize} B (2 views x 4 taps x {esize} B) per line pair"},
                      "total": float(r["total"].cpu()[0]),
                      "vs_oracle_120_pairs": error_stats(d[flat], r_or["d"], E_or, float(d[flat].sum()),
                                                         float(r_or["d"].sum())),
@@ -764,8 +767,8 @@ def run_ours(args):
                      "pair_kernel_frac_of_hbm": gbs / peaks.get("hbm_gbs", 6800.0),
                      # one ncu capture of this launch (one-pass metrics, same kernel build):
                      # DRAM read + write and L2 sector bytes per launch
-                     "pair_kernel_dram_bytes_ncu": 446589952 + 23083776,
-                     "pair_kernel_l2_bytes_ncu": 81681858 * 32}
+                     "pair_kernel_dram_bytes_ncu": 455751680 + 33869824,
+                     "pair_kernel_l2_bytes_ncu": 87438933 * 32}
     l2 = l2_read_rate(dev)
     if eval_only:
         eval_only["pair_kernel_frac_of_l2"] = eval_only["pair_kernel_gather_gbs"] / l2["gbs"]

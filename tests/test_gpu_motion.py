@@ -72,7 +72,11 @@ def test_spline_job_equals_host_loop():
     # node values: two FP32 gradient evaluations (separately compiled per-sample code,
     # ~1e-6 apart) and the oracle's difference Jacobian, over six steps
     np.testing.assert_allclose(served["nodes"], nodes, rtol=1e-4, atol=1e-7)
-    np.testing.assert_allclose(served["motion"], mo.spline_motion(n, nodes, base, mask), rtol=1e-4, atol=1e-7)
+    # the served motion is the library's FP64 spline of its own nodes (Akima's weights
+    # amplify the node differences above where slopes nearly agree, so the motion is
+    # compared at the served nodes)
+    np.testing.assert_allclose(served["motion"], mo.spline_motion(n, served["nodes"], base, mask), rtol=1e-9,
+                               atol=1e-12)
     # parameters outside the mask stay at motion0
     assert np.array_equal(served["motion"][:, [0, 3, 4]], base[:, [0, 3, 4]])
 
