@@ -845,6 +845,67 @@ __device__ __forceinline__ float tile_adjoint_series(const float4* __restrict__ 
   return Sa - Sb;
 }
 
+// Two tiles at once (the lane's samples of tiles u and u + 1, offsets q from the anchors
+// of each): positions of all four view-samples first, then all sixteen taps, so that the
+// gathers of both tiles are in flight together.  Returns false, with nothing computed, if
+// some lane's row leaves [0, n_alpha - 2] in either tile (the caller then takes the
+// tiles one at a time).
+template <typename T, int NT>
+__device__ __forceinline__ bool tile_adjoint_series2(const float4* __restrict__ ra0, const float4* __restrict__ rb0,
+                                                     const float4* __restrict__ ra1, const float4* __restrict__ rb1,
+                                                     const LaneGeom& q, const T* __restrict__ sa,
+                                                     const T* __restrict__ sb, float sca, float scb, int n_alpha,
+                                                     int n_s, float inv_dalpha, float inv_ds_f,
+                                                     const float4* __restrict__ lpa0, const float4* __restrict__ lpb0,
+                                                     const float4* __restrict__ lpa1, const float4* __restrict__ lpb1,
+                                                     float& dd0, float (&ga0)[3], float (&gb0)[3], float& dd1,
+                                                     float (&ga1)[3], float (&gb1)[3]) {
+  unsigned ma0, mb0, ma1, mb1;
+  int na0, nb0, na1, nb1;
+  float fa0, fs0, fb0, gs0, fa1, fs1, fb1, gs1;
+  series_position<NT>(ra0, q, ma0, na0, fa0, fs0);
+  series_position<NT>(rb0, q, mb0, nb0, fb0, gs0);
+  series_position<NT>(ra1, q, ma1, na1, fa1, fs1);
+  series_position<NT>(rb1, q, mb1, nb1, fb1, gs1);
+  const unsigned last = (unsigned)(n_alpha - 1);
+  if (__any_sync(0xffffffffu, ma0 >= last || mb0 >= last || ma1 >= last || mb1 >= last)) return false;
+  float l0, l1, l2;
+  tile_line(lpa0, q.cd, q.sd, l0, l1, l2);
+  const float Sa0 = sample_grad_rows(sa, n_s, ma0, na0, fa0, fs0, ra0[1].x, inv_dalpha, inv_ds_f, l0, l1, l2, sca, ga0);
+  tile_line(lpb0, q.cd, q.sd, l0, l1, l2);
+  const float Sb0 = sample_grad_rows(sb, n_s, mb0, nb0, fb0, gs0, rb0[1].x, inv_dalpha, inv_ds_f, l0, l1, l2, scb, gb0);
+  tile_line(lpa1, q.cd, q.sd, l0, l1, l2);
+  const float Sa1 = sample_grad_rows(sa, n_s, ma1, na1, fa1, fs1, ra1[1].x, inv_dalpha, inv_ds_f, l0, l1, l2, sca, ga1);
+  tile_line(lpb1, q.cd, q.sd, l0, l1, l2);
+  const float Sb1 = sample_grad_rows(sb, n_s, mb1, nb1, fb1, gs1, rb1[1].x, inv_dalpha, inv_ds_f, l0, l1, l2, scb, gb1);
+  dd0 = Sa0 - Sb0;
+  dd1 = Sa1 - Sb1;
+  return true;
+}
+
+template <typename T>
+__device__ __forceinline__ bool tile_adjoint2(const float4* __restrict__ ra0, const float4* __restrict__ rb0,
+                                              const float4* __restrict__ ra1, const float4* __restrict__ rb1,
+                                              const LaneGeom& q, const T* __restrict__ sa, const T* __restrict__ sb,
+                                              float sca, float scb, int n_alpha, int n_s, float inv_dalpha,
+                                              float inv_ds_f, const float4* __restrict__ lpa0,
+                                              const float4* __restrict__ lpb0, const float4* __restrict__ lpa1,
+                                              const float4* __restrict__ lpb1, float& dd0, float (&ga0)[3],
+                                              float (&gb0)[3], float& dd1, float (&ga1)[3], float (&gb1)[3]) {
+  const float n0 = ra0[1].w, n1 = rb0[1].w, n2 = ra1[1].w, n3 = rb1[1].w;
+  if (n0 == 0.0f || n1 == 0.0f || n2 == 0.0f || n3 == 0.0f) return false;  // a closed-form anchor
+  const float nt = fmaxf(fmaxf(n0, n1), fmaxf(n2, n3));
+#define ECC_ADJ2(NT_)                                                                                          \
+  return tile_adjoint_series2<T, NT_>(ra0, rb0, ra1, rb1, q, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha,        \
+                                      inv_ds_f, lpa0, lpb0, lpa1, lpb1, dd0, ga0, gb0, dd1, ga1, gb1)
+  if (nt <= 3.0f) ECC_ADJ2(3);
+  if (nt <= 4.0f) ECC_ADJ2(4);
+  if (nt <= 6.0f) ECC_ADJ2(6);
+  if (nt <= 8.0f) ECC_ADJ2(8);
+  ECC_ADJ2(12);
+#undef ECC_ADJ2
+}
+
 template <typename T>
 __device__ __forceinline__ float tile_adjoint(const float4* __restrict__ ra, const float4* __restrict__ rb,
                                              const LaneGeom& q, const T* __restrict__ sa, const T* __restrict__ sb,
@@ -957,7 +1018,44 @@ __device__ __forceinline__ double pair_warp_adjoint(const PairArgs& g, long long
       __syncwarp();
       const int tmax = min(16, n_tiles - t0);
       const int tfull = (t0 + tmax == n_tiles && n_last != 32) ? tmax - 1 : tmax;
-      for (int tt = 0; tt < tfull; ++tt) {
+      int tt = 0;
+      if (FAST) {
+        // two full tiles per iteration: their gathers are in flight together
+        for (; tt + 1 < tfull; tt += 2) {
+          const int t = t0 + tt;
+          float dd0, dd1, ga0[3], gb0[3], ga1[3], gb1[3];
+          if (!tile_adjoint2<T>(recw + kRec * tt, recw + kRec * (16 + tt), recw + kRec * (tt + 1),
+                                recw + kRec * (17 + tt), qf, sa, sb, sca, scb, n_alpha, n_s, inv_dalpha, inv_ds_f,
+                                lpw + 2 * tt, lpw + 2 * (16 + tt), lpw + 2 * (tt + 1), lpw + 2 * (17 + tt), dd0, ga0,
+                                gb0, dd1, ga1, gb1)) {
+            for (int u = 0; u < 2; ++u) {
+              const int k = 32 * (t + u) + lane;
+              one_tile(t + u, qf, (unsigned)(k - r0lo) < len0 || (unsigned)(k - r1lo) < len1);
+            }
+            continue;
+          }
+          for (int u = 0; u < 2; ++u) {
+            const int k = 32 * (t + u) + lane;
+            const bool valid = (unsigned)(k - r0lo) < len0 || (unsigned)(k - r1lo) < len1;
+            const float4 ctd = ct[t + u];
+            const float ckx = ctd.x * qf.cd - ctd.y * qf.sd, cky = ctd.x * qf.sd + ctd.y * qf.cd;
+            const float dd = u ? dd1 : dd0;
+            acc += valid ? dd * dd : 0.0f;
+            if (valid) {
+              const float w2 = 2.0f * dd;
+#pragma unroll
+              for (int i = 0; i < 3; ++i) {
+                const float a = u ? ga1[i] : ga0[i], b = u ? gb1[i] : gb0[i];
+                G[2 * i] = fmaf(w2 * a, ckx, G[2 * i]);
+                G[2 * i + 1] = fmaf(w2 * a, cky, G[2 * i + 1]);
+                G[6 + 2 * i] = fmaf(-w2 * b, ckx, G[6 + 2 * i]);
+                G[6 + 2 * i + 1] = fmaf(-w2 * b, cky, G[6 + 2 * i + 1]);
+              }
+            }
+          }
+        }
+      }
+      for (; tt < tfull; ++tt) {
         const int k = 32 * (t0 + tt) + lane;
         one_tile(t0 + tt, qf, (unsigned)(k - r0lo) < len0 || (unsigned)(k - r1lo) < len1);
       }
@@ -1029,9 +1127,10 @@ __device__ __forceinline__ void pair_block(const PairArgs& g, long long blk, dou
 }
 
 // The forward kernel runs four blocks per SM (64 registers: more gathers in flight);
-// the adjoint keeps three (its per-sample state is larger).
+// the adjoint runs two (127 registers, no spills): it takes two tiles per iteration, so
+// each warp has twice the gathers in flight and needs fewer resident warps.
 template <typename T, bool GRAD>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, GRAD ? 3 : 4) ecc_pair_kernel(PairArgs g) {
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, GRAD ? 2 : 4) ecc_pair_kernel(PairArgs g) {
   __shared__ double e_warp[kWarpsPerBlock];
   __shared__ float4 recs[kWarpsPerBlock * 32 * kRec];         // anchor records, 5.5 KB per warp
   __shared__ float4 lps[GRAD ? kWarpsPerBlock * 64 : 1];      // the adjoint's tile lines, 1 KB per warp
