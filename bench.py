@@ -282,22 +282,27 @@ def serving_leg(args, c2_scan):
                                      want_per_pair=False)["total"].cpu()[0])
         acc.append(abs(results[j]["total_first"] - ref) / abs(ref))
     # the same jobs, one after the other, through plain calls on one stream: upload,
-    # precompute, n_iters x (ecc_evaluate_grad, step), final ecc_evaluate
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _, det, P, I, K, th in jobs:
-        W, H, _, na, ns, _ = SERVE_DETECTORS[det]
-        Pd, Id = P.cuda(non_blocking=True), I.cuda(non_blocking=True)
-        S, scales = ecc.ecc_precompute_radon_derivative(ctx, Pd, Id, na, ns, dtype=torch.float16)
-        del Id
-        theta = torch.from_numpy(th).cuda()
-        for _ in range(iters):
-            g = ecc.ecc_evaluate_grad(ctx, Pd, S, W, H, K, motion=theta, scales=scales, want_per_pair=False)["grad"]
-            theta -= step * g
-        ecc.ecc_evaluate(ctx, Pd, S, W, H, K, motion=theta, scales=scales, want_per_pair=False)
-        del S, scales
-    torch.cuda.synchronize()
-    plain_s = time.perf_counter() - t0
+    # precompute, n_iters x (ecc_evaluate_grad, step), final ecc_evaluate.  Two passes:
+    # the first also pays one-time costs (first allocations of each job shape, first
+    # launches; about a second after the served run); the second is reported.
+    plain_passes = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _, det, P, I, K, th in jobs:
+            W, H, _, na, ns, _ = SERVE_DETECTORS[det]
+            Pd, Id = P.cuda(non_blocking=True), I.cuda(non_blocking=True)
+            S, scales = ecc.ecc_precompute_radon_derivative(ctx, Pd, Id, na, ns, dtype=torch.float16)
+            del Id
+            theta = torch.from_numpy(th).cuda()
+            for _ in range(iters):
+                g = ecc.ecc_evaluate_grad(ctx, Pd, S, W, H, K, motion=theta, scales=scales, want_per_pair=False)["grad"]
+                theta -= step * g
+            ecc.ecc_evaluate(ctx, Pd, S, W, H, K, motion=theta, scales=scales, want_per_pair=False)
+            del S, scales
+        torch.cuda.synchronize()
+        plain_passes.append(time.perf_counter() - t0)
+    plain_s = plain_passes[-1]
     ctx.close()
     return {"metric": "ECC line-pair samples/s, served (FP16 storage, with gradients)", "value": lp / wall,
             "unit": UNIT, "jobs": len(results), "wall_s": wall, "arrival_rate_per_s": args.serve_rate,
@@ -311,8 +316,11 @@ def serving_leg(args, c2_scan):
                                "note": "device time of each part over the wall time; admissions overlap rounds, so "
                                        "the parts may sum above 1"},
             "plain_calls_same_jobs": {"value": lp / plain_s, "unit": UNIT, "wall_s": plain_s,
+                                      "first_pass_wall_s": plain_passes[0],
                                       "how": "the same jobs back to back, no arrival process: upload, precompute, "
-                                             f"{iters} x (ecc_evaluate_grad + step), ecc_evaluate, one stream"},
+                                             f"{iters} x (ecc_evaluate_grad + step), ecc_evaluate, one stream; "
+                                             "second of two passes (the first also pays one-time allocations and "
+                                             "launches)"},
             "max_jobs_per_round": st["max_batch"], "iterations_per_job": iters, "step": step,
             "fp16_vs_fp32_total_rel_err": {"jobs": len(acc), "max": float(max(acc)) if acc else None},
             "jobs_mix": "detector uniform {256^2, 620x480, 976^2}, views U{50..500}, kappa U{256..1024}, "
