@@ -803,6 +803,8 @@ def run_ours(args):
         accuracy = error_stats(r32["per_pair"][:, 0].cpu().numpy(), oracle["d"], oracle["E"],
                                float(r32["total"].cpu()[0]), oracle["total"])
         accuracy["oracle_total"] = oracle["total"]
+        # N_kappa of every pair (integer sample ranges of the set-up) against the oracle's
+        accuracy["nkappa_mismatches"] = int(np.count_nonzero(r32["nkappa"].cpu().numpy() != np.asarray(oracle["nk"])))
     forms = None
     if not args.no_storage_forms:
         forms = storage_forms(ctx, P, images, cfg, result_total, oracle=oracle, l2_gbs=l2["gbs"])

@@ -91,6 +91,88 @@ __host__ __device__ __forceinline__ df df_rsqrt(df a) {
   return df_mul_f(t, y0);
 }
 
+// a / b for an FP32 divisor (one correction of the FP32 quotient).
+__host__ __device__ __forceinline__ df df_div_f(df a, float b) {
+  const float q1 = a.hi / b;
+  const df p = df_two_prod(q1, b);
+  const float r = ((a.hi - p.hi) - p.lo) + a.lo;
+  return df_fast_two_sum(q1, r / b);
+}
+
+__host__ __device__ __forceinline__ bool df_lt0(df a) { return a.hi < 0.0f || (a.hi == 0.0f && a.lo < 0.0f); }
+
+// pi as a double-float pair; pi / 2 in three FP32 parts (for the range reduction);
+// all folded at compile time (scalar constexpr values).
+constexpr double kDfPi = 3.14159265358979323846;
+constexpr float kDfPiHi = (float)kDfPi;
+constexpr float kDfPiLo = (float)(kDfPi - (double)kDfPiHi);
+constexpr double kDfPio2 = 1.57079632679489661923;
+constexpr float kDfPio2A = (float)kDfPio2;
+constexpr float kDfPio2B = (float)(kDfPio2 - (double)kDfPio2A);
+constexpr float kDfPio2C = (float)((kDfPio2 - (double)kDfPio2A) - (double)kDfPio2B);
+constexpr float kDf2OverPi = (float)(2.0 / kDfPi);
+
+__host__ __device__ inline df df_pi() { return df{kDfPiHi, kDfPiLo}; }
+
+// 1 / n! at compile time.
+template <int N>
+struct DfInvFact {
+  static constexpr double v = DfInvFact<N - 1>::v / (double)N;
+};
+template <>
+struct DfInvFact<0> {
+  static constexpr double v = 1.0;
+};
+
+// Horner forms of sum_{j >= k} (-1)^j x^j / (2j + 1)! (sin r / r, x = r^2, to j = 8)
+// and of sum_{j >= k} (-1)^j x^j / (2j)! (cos r, to j = 9), coefficients as
+// double-float constants.
+template <int k>
+__host__ __device__ __forceinline__ df df_sin_poly(df x) {
+  constexpr double c = ((k & 1) ? -1.0 : 1.0) * DfInvFact<2 * k + 1>::v;
+  constexpr float ch = (float)c, cl = (float)(c - (double)ch);
+  if constexpr (k == 8)
+    return df{ch, cl};
+  else
+    return df_add(df_mul(df_sin_poly<k + 1>(x), x), df{ch, cl});
+}
+template <int k>
+__host__ __device__ __forceinline__ df df_cos_poly(df x) {
+  constexpr double c = ((k & 1) ? -1.0 : 1.0) * DfInvFact<2 * k>::v;
+  constexpr float ch = (float)c, cl = (float)(c - (double)ch);
+  if constexpr (k == 9)
+    return df{ch, cl};
+  else
+    return df_add(df_mul(df_cos_poly<k + 1>(x), x), df{ch, cl});
+}
+
+// sin and cos of a double-float angle |a| <= 4: a = q pi/2 + r with |r| <= pi/4 (q an
+// integer, r in double-float), Taylor series of sin r to r^17 and of cos r to r^18
+// (truncation below 1e-16 at |r| = pi/4), then the quadrant.
+__host__ __device__ inline void df_sincos(df a, df* s, df* c) {
+  const float q = rintf(a.hi * kDf2OverPi);
+  const df qp = df_add(df_add(df_two_prod(q, kDfPio2A), df_two_prod(q, kDfPio2B)), df{q * kDfPio2C, 0.0f});
+  const df r = df_sub(a, qp);
+  const df x = df_mul(r, r);
+  const df sr = df_mul(df_sin_poly<0>(x), r), cr = df_cos_poly<0>(x);
+  const int qi = ((int)q) & 3;
+  *s = qi == 0 ? sr : (qi == 1 ? cr : (qi == 2 ? df_neg(sr) : df_neg(cr)));
+  *c = qi == 0 ? cr : (qi == 1 ? df_neg(sr) : (qi == 2 ? df_neg(cr) : sr));
+}
+
+// atan2(y, x) in double-float: the FP32 angle t0 and its sin and cos, then the
+// remaining turn d = atan((y cos t0 - x sin t0) / (x cos t0 + y sin t0)); |d| is a few
+// 1e-7, so d itself (error d^3 / 3) completes it.  atan2(0, 0) = 0.
+__host__ __device__ inline df df_atan2(df y, df x) {
+  if (y.hi == 0.0f && x.hi == 0.0f) return df{0.0f, 0.0f};
+  const float t0 = atan2f(y.hi, x.hi);
+  df s0, c0;
+  df_sincos(df{t0, 0.0f}, &s0, &c0);
+  const df num = df_sub(df_mul(y, c0), df_mul(x, s0));
+  const df den = df_add(df_mul(x, c0), df_mul(y, s0));
+  return df_add(df{t0, 0.0f}, df_mul(num, df_recip(den)));
+}
+
 // floor of a double-float value and the FP32 fraction in [0, 1).
 __host__ __device__ __forceinline__ float df_floor_frac(df a, float* frac) {
   float n = floorf(a.hi);

@@ -23,6 +23,8 @@ struct ViewRec {
   double cofc[9];  // cofactor matrix of M, rows; third row re-expressed for
                    // detector coordinates centred at ((W-1)/2, (H-1)/2)
   double u0, v0, D;  // principal point and source-detector distance [px]
+  float qdf[30];     // C, up, cofc (15 values) as double-float (hi, lo) pairs, for the
+                     // per-pair set-up on the FP32 pipes
   int status;        // 0 ok, 1 degenerate P
   int pad;
 };
@@ -42,11 +44,10 @@ struct ViewTanP {
 
 // Per-pair set-up (FP64 geometry, integer sample ranges).
 struct PairRec {
-  double A[2][6];   // per view (a, b): l_centred(kappa) = A (cos kappa, sin kappa), 3x2 row-major
-  float Af[2][12];  // A as double-float pairs (hi, lo) per entry, for the pair kernel's anchors
+  float Af[2][12];  // per view (a, b): l_centred(kappa) = A (cos kappa, sin kappa), A 3x2 row-major,
+                    // each entry a double-float pair (hi, lo)
   float dk_hi, dk_lo;  // Delta kappa as a double-float pair
   double c0[2];     // direction of the first sample, (k + 1/2) = 1/2, in the (w, v) frame
-  double rot[2];    // cos, sin of one sample step Delta kappa
   double dk;        // Delta kappa
   int32_t a, b;     // view indices
   int32_t r0lo, r0hi, r1lo, r1hi;  // valid samples: [r0lo, r0hi) U [r1lo, r1hi)

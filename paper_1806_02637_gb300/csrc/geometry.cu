@@ -1,4 +1,5 @@
-// Per-view and per-pair FP64 set-up of the ECC path (no matrix inverse anywhere).
+// Per-view and per-pair set-up of the ECC path (no matrix inverse anywhere): FP64 per
+// view, double-float vector algebra with FP64 angles per pair.
 //
 //  view_setup_kernel  one thread per view: rigid motion P' = P T(theta), scaling,
 //                     source as the meet of the rows of P (Eq. 4/5), cofactor
@@ -105,38 +106,9 @@ __host__ __device__ bool view_geometry(const T* Pm, int W, int H, T* Pn, T* C, T
   return ok;
 }
 
-// Frame of the pencil of epipolar planes around the baseline C_a -> C_b:
-// u = baseline direction, w = (up_a + up_b) made orthogonal to u (the world axis
-// least aligned with u if that is degenerate), v = w x u; the plane at kappa has
-// normal cos(kappa) w + sin(kappa) v.  Returns false for coincident sources.
-template <class T>
-__host__ __device__ bool pencil_frame(const T* Ca, const T* Cb, const T* upa, const T* upb, T* w, T* v) {
-  T d[3] = {Cb[0] - Ca[0], Cb[1] - Ca[1], Cb[2] - Ca[2]};
-  const T nd = sqrt(dot3(d, d));
-  if (!(value(nd) > 0.0)) return false;
-  T u[3];
-  for (int k = 0; k < 3; ++k) u[k] = d[k] / nd;
-  T rr[3] = {upa[0] + upb[0], upa[1] + upb[1], upa[2] + upb[2]};
-  const T ru = dot3(rr, u);
-  for (int k = 0; k < 3; ++k) w[k] = rr[k] - ru * u[k];
-  T nw = sqrt(dot3(w, w));
-  if (value(nw) < 1e-6) {
-    // the first axis within 1e-9 of the smallest |u_k|: ties are not left to rounding
-    const double best = fmin(fabs(value(u[0])), fmin(fabs(value(u[1])), fabs(value(u[2]))));
-    int ax = 0;
-    while (fabs(value(u[ax])) > best + 1e-9) ++ax;
-    const T ui = u[ax];
-    for (int k = 0; k < 3; ++k) w[k] = T(k == ax ? 1.0 : 0.0) - ui * u[k];
-    nw = sqrt(dot3(w, w));
-  }
-  for (int k = 0; k < 3; ++k) w[k] = w[k] / nw;
-  cross3(w, u, v);
-  return true;
-}
-
-// Reverse mode of pencil_frame (FP64): given gw = d e / d w and gv = d e / d v, adds
-// d e / d (Ca, Cb, upa, upb) to gCa, gCb and gup (the same for both up axes, which
-// enter as their sum); also returns w and v.  Each step's adjoint follows from its
+// Reverse mode of the pencil frame (FP64; the frame that pencil_frame_df builds):
+// given gw = d e / d w and gv = d e / d v, adds d e / d (Ca, Cb, upa, upb) to gCa, gCb
+// and gup (the same for both up axes, which enter as their sum); also returns w and v.  Each step's adjoint follows from its
 // forward rule: v = w x u gives w' += u x v', u' += v' x w; y = x / |x| gives
 // x' = (y' - (y'.y) y) / |x|; w_t = r - (r.u) u gives r' = w_t' - (w_t'.u) u and
 // u' -= (w_t'.u) r + (r.u) w_t' (for the fallback axis e: u' -= (w_t'.u) e_ax + u_ax w_t').
@@ -208,6 +180,11 @@ __host__ __device__ ViewRec setup_view(const double* P, const double* motion, in
   r.pad = 0;
   const bool ok = view_geometry(Pm, W, H, r.P, r.C, r.up, r.cofc, &r.u0, &r.v0, &r.D);
   r.status = ok ? 0 : 1;
+  for (int k = 0; k < 15; ++k) {
+    const df q = df_from_double(k < 3 ? r.C[k] : (k < 6 ? r.up[k - 3] : r.cofc[k - 6]));
+    r.qdf[2 * k] = q.hi;
+    r.qdf[2 * k + 1] = q.lo;
+  }
   return r;
 }
 
@@ -282,54 +259,113 @@ __global__ void view_tangent_P_kernel(int n_views, const double* __restrict__ P,
 
 namespace {
 
+// Double-float vector helpers of the per-pair set-up.
+__host__ __device__ inline df qget(const ViewRec& v, int k) { return df{v.qdf[2 * k], v.qdf[2 * k + 1]}; }
+__host__ __device__ inline df df_dot3(const df* a, const df* b) {
+  return df_add(df_add(df_mul(a[0], b[0]), df_mul(a[1], b[1])), df_mul(a[2], b[2]));
+}
+__host__ __device__ inline df df_cross2(df ax, df ay, df bx, df by) { return df_sub(df_mul(ax, by), df_mul(ay, bx)); }
+__host__ __device__ inline df df_sel(bool c, df a, df b) { return c ? a : b; }
+
+// Frame of the pencil of epipolar planes around the baseline C_a -> C_b, in
+// double-float: u = baseline direction, w = (up_a + up_b) made orthogonal to u (below
+// |w| = 1e-6 the world axis least aligned with u, the first within 1e-9 of the
+// smallest |u_k| so that ties are not left to rounding), v = w x u; the plane at kappa
+// has normal cos(kappa) w + sin(kappa) v.  Normalisations are products by reciprocal
+// square roots.  Returns false for coincident sources.
+__host__ __device__ bool pencil_frame_df(const ViewRec& va, const ViewRec& vb, df* w, df* v) {
+  df d[3], rr[3], u[3];
+  for (int k = 0; k < 3; ++k) {
+    d[k] = df_sub(qget(vb, k), qget(va, k));
+    rr[k] = df_add(qget(va, 3 + k), qget(vb, 3 + k));
+  }
+  const df nd2 = df_dot3(d, d);
+  if (!(nd2.hi > 0.0f)) return false;
+  const df ind = df_rsqrt(nd2);
+  for (int k = 0; k < 3; ++k) u[k] = df_mul(d[k], ind);
+  const df ru = df_dot3(rr, u);
+  for (int k = 0; k < 3; ++k) w[k] = df_sub(rr[k], df_mul(ru, u[k]));
+  df nw2 = df_dot3(w, w);
+  if (nw2.hi < 1e-12f) {
+    // the first axis within 1e-9 of the smallest |u_k|: ties are not left to rounding
+    const double ua[3] = {fabs(df_to_double(u[0])), fabs(df_to_double(u[1])), fabs(df_to_double(u[2]))};
+    const double best = fmin(ua[0], fmin(ua[1], ua[2]));
+    const int ax = ua[0] <= best + 1e-9 ? 0 : (ua[1] <= best + 1e-9 ? 1 : 2);
+    const df ui = ax == 0 ? u[0] : (ax == 1 ? u[1] : u[2]);
+    for (int k = 0; k < 3; ++k) w[k] = df_sub(df{k == ax ? 1.0f : 0.0f, 0.0f}, df_mul(ui, u[k]));
+    nw2 = df_dot3(w, w);
+  }
+  const df inw = df_rsqrt(nw2);
+  for (int k = 0; k < 3; ++k) w[k] = df_mul(w[k], inw);
+  v[0] = df_cross2(w[1], w[2], u[1], u[2]);
+  v[1] = df_cross2(w[2], w[0], u[2], u[0]);
+  v[2] = df_cross2(w[0], w[1], u[0], u[1]);
+  return true;
+}
+
 // Valid arc of the pencil for one view: the plane at kappa (c = (cos, sin)) meets
 // the detector rectangle iff the values g_c . c at the four corners do not all have
 // the same strict sign, g_c = A^T x_c.  If the g_c lie in a half plane (epipole
 // outside), the valid directions (mod pi) run counter-clockwise from rot90(g_min)
-// over the angle between the extreme g's; otherwise every plane is valid.
-__host__ __device__ double view_arc(const double* A, int W, int H, double* clo) {
-  const double xs[4] = {-0.5 * W, 0.5 * W, 0.5 * W, -0.5 * W};
-  const double ys[4] = {-0.5 * H, -0.5 * H, 0.5 * H, 0.5 * H};
-  double g[4][2];
+// over the angle between the extreme g's; otherwise every plane is valid.  The
+// corner values, the sign tests (each cross product once, with its antisymmetry for
+// the reversed order) and the angle run in double-float.
+__host__ __device__ df view_arc(const df* A, int W, int H, df* clo) {
+  const float hw = 0.5f * (float)W, hh = 0.5f * (float)H;  // exact
+  const float xs[4] = {-hw, hw, hw, -hw};
+  const float ys[4] = {-hh, -hh, hh, hh};
+  df sc = df_mul(A[0], A[0]);
+  for (int k = 1; k < 6; ++k) sc = df_add(sc, df_mul(A[k], A[k]));
+  df gx[4], gy[4], n2[4];
   bool degenerate = false;
+#pragma unroll
   for (int c = 0; c < 4; ++c) {
-    g[c][0] = A[0] * xs[c] + A[2] * ys[c] + A[4];
-    g[c][1] = A[1] * xs[c] + A[3] * ys[c] + A[5];
-    const double n2 = g[c][0] * g[c][0] + g[c][1] * g[c][1];
-    const double sc = A[0] * A[0] + A[1] * A[1] + A[2] * A[2] + A[3] * A[3] + A[4] * A[4] + A[5] * A[5];
-    if (!(n2 > 1e-28 * sc)) degenerate = true;
+    gx[c] = df_add(df_add(df_mul_f(A[0], xs[c]), df_mul_f(A[2], ys[c])), A[4]);
+    gy[c] = df_add(df_add(df_mul_f(A[1], xs[c]), df_mul_f(A[3], ys[c])), A[5]);
+    n2[c] = df_add(df_mul(gx[c], gx[c]), df_mul(gy[c], gy[c]));
+    if (!(n2[c].hi > 1e-28f * sc.hi)) degenerate = true;
   }
-  int imin = -1, imax = -1;
-  for (int i = 0; i < 4 && !degenerate; ++i) {
-    bool is_min = true, is_max = true;
-    for (int j = 0; j < 4; ++j) {
-      if (g[i][0] * g[j][1] - g[i][1] * g[j][0] < 0.0) is_min = false;
-      if (g[j][0] * g[i][1] - g[j][1] * g[i][0] < 0.0) is_max = false;
-    }
-    if (is_min && imin < 0) imin = i;
-    if (is_max && imax < 0) imax = i;
-  }
+  // cross products g_i x g_j (i < j); g_j x g_i = -(g_i x g_j)
+  const float c01 = df_cross2(gx[0], gy[0], gx[1], gy[1]).hi, c02 = df_cross2(gx[0], gy[0], gx[2], gy[2]).hi;
+  const float c03 = df_cross2(gx[0], gy[0], gx[3], gy[3]).hi, c12 = df_cross2(gx[1], gy[1], gx[2], gy[2]).hi;
+  const float c13 = df_cross2(gx[1], gy[1], gx[3], gy[3]).hi, c23 = df_cross2(gx[2], gy[2], gx[3], gy[3]).hi;
+  // corner i is the minimum if g_i x g_j >= 0 for every j, the maximum if <= 0
+  const bool mn0 = c01 >= 0.0f && c02 >= 0.0f && c03 >= 0.0f, mx0 = c01 <= 0.0f && c02 <= 0.0f && c03 <= 0.0f;
+  const bool mn1 = -c01 >= 0.0f && c12 >= 0.0f && c13 >= 0.0f, mx1 = -c01 <= 0.0f && c12 <= 0.0f && c13 <= 0.0f;
+  const bool mn2 = -c02 >= 0.0f && -c12 >= 0.0f && c23 >= 0.0f, mx2 = -c02 <= 0.0f && -c12 <= 0.0f && c23 <= 0.0f;
+  const bool mn3 = -c03 >= 0.0f && -c13 >= 0.0f && -c23 >= 0.0f, mx3 = -c03 <= 0.0f && -c13 <= 0.0f && -c23 <= 0.0f;
+  const int imin = mn0 ? 0 : (mn1 ? 1 : (mn2 ? 2 : (mn3 ? 3 : -1)));
+  const int imax = mx0 ? 0 : (mx1 ? 1 : (mx2 ? 2 : (mx3 ? 3 : -1)));
   if (degenerate || imin < 0 || imax < 0) {
-    clo[0] = 0.0;
-    clo[1] = -1.0;
-    return kPi;
+    clo[0] = df{0.0f, 0.0f};
+    clo[1] = df{-1.0f, 0.0f};
+    return df_pi();
   }
-  const double cr = g[imin][0] * g[imax][1] - g[imin][1] * g[imax][0];
-  const double dt = g[imin][0] * g[imax][0] + g[imin][1] * g[imax][1];
-  double phi = atan2(cr, dt);
-  if (phi < 0.0) phi = 0.0;
-  const double ng = sqrt(g[imin][0] * g[imin][0] + g[imin][1] * g[imin][1]);
-  clo[0] = -g[imin][1] / ng;
-  clo[1] = g[imin][0] / ng;
+  // (scalars and selects only: no dynamically indexed local arrays)
+  const df ax_ = df_sel(imin == 0, gx[0], df_sel(imin == 1, gx[1], df_sel(imin == 2, gx[2], gx[3])));
+  const df ay_ = df_sel(imin == 0, gy[0], df_sel(imin == 1, gy[1], df_sel(imin == 2, gy[2], gy[3])));
+  const df an2 = df_sel(imin == 0, n2[0], df_sel(imin == 1, n2[1], df_sel(imin == 2, n2[2], n2[3])));
+  const df bx_ = df_sel(imax == 0, gx[0], df_sel(imax == 1, gx[1], df_sel(imax == 2, gx[2], gx[3])));
+  const df by_ = df_sel(imax == 0, gy[0], df_sel(imax == 1, gy[1], df_sel(imax == 2, gy[2], gy[3])));
+  const df cr = df_cross2(ax_, ay_, bx_, by_);
+  const df dt = df_add(df_mul(ax_, bx_), df_mul(ay_, by_));
+  df phi = df_atan2(cr, dt);
+  if (df_lt0(phi)) phi = df{0.0f, 0.0f};
+  const df ing = df_rsqrt(an2);
+  clo[0] = df_neg(df_mul(ay_, ing));
+  clo[1] = df_mul(ax_, ing);
   return phi;
 }
 
 }  // namespace
 
-// Per-pair set-up (FP64): frame, kappa -> line maps, valid arcs, the sampled arc,
-// the integer ranges of valid samples and the tile-centre directions (ctile,
-// n_tiles entries).  With previous != NULL the sampling of *previous is kept and
-// only the maps follow the geometry.
+// Per-pair set-up: frame, kappa -> line maps, valid arcs, the sampled arc, the
+// integer ranges of valid samples and the tile-centre directions (ctile, n_tiles
+// entries).  With previous != NULL the sampling of *previous is kept and only the maps
+// follow the geometry.  GB300 issues FP64 at 1/64 of the FP32 rate, so the vector
+// algebra (frame, maps, corner values) runs in double-float on the FP32 pipes from the
+// views' double-float copies; the angles (atan2, sincos), the step and the integer
+// ranges stay in FP64.
 __host__ __device__ PairRec setup_pair(int a, int b, int n_views, const ViewRec* views, int W, int H, int K,
                                        float4* ctile, int n_tiles, const PairRec* previous) {
   const bool reuse_sampling = previous != nullptr;
@@ -349,20 +385,23 @@ __host__ __device__ PairRec setup_pair(int a, int b, int n_views, const ViewRec*
   for (int i = 0; i < 24; ++i) (&r.Af[0][0])[i] = 0.0f;
   r.c0[0] = 1.0;
   r.c0[1] = 0.0;
-  r.rot[0] = 1.0;
-  r.rot[1] = 0.0;
-  for (int i = 0; i < 12; ++i) (&r.A[0][0])[i] = 0.0;
   const ViewRec& va = views[a];
   const ViewRec& vb = views[b];
-  double w[3] = {0, 0, 0}, v[3] = {0, 0, 0};
-  bool ok = in_range && va.status == 0 && vb.status == 0 && a != b &&
-            pencil_frame(va.C, vb.C, va.up, vb.up, w, v);
+  df w[3], v[3];
+  df Ad[2][6];
+  bool ok = in_range && va.status == 0 && vb.status == 0 && a != b && pencil_frame_df(va, vb, w, v);
   if (ok) {
     const ViewRec* vv[2] = {&va, &vb};
     for (int s = 0; s < 2; ++s)
       for (int i = 0; i < 3; ++i) {
-        r.A[s][2 * i + 0] = dot3(vv[s]->cofc + 3 * i, w);
-        r.A[s][2 * i + 1] = dot3(vv[s]->cofc + 3 * i, v);
+        const df row[3] = {qget(*vv[s], 6 + 3 * i), qget(*vv[s], 7 + 3 * i), qget(*vv[s], 8 + 3 * i)};
+        Ad[s][2 * i + 0] = df_dot3(row, w);
+        Ad[s][2 * i + 1] = df_dot3(row, v);
+      }
+    for (int s = 0; s < 2; ++s)
+      for (int i = 0; i < 6; ++i) {
+        r.Af[s][2 * i] = Ad[s][i].hi;
+        r.Af[s][2 * i + 1] = Ad[s][i].lo;
       }
   }
   if (ok && reuse_sampling) {
@@ -372,8 +411,8 @@ __host__ __device__ PairRec setup_pair(int a, int b, int n_views, const ViewRec*
     r.dk = old.dk;
     r.c0[0] = old.c0[0];
     r.c0[1] = old.c0[1];
-    r.rot[0] = old.rot[0];
-    r.rot[1] = old.rot[1];
+    r.dk_hi = old.dk_hi;
+    r.dk_lo = old.dk_lo;
     r.r0lo = old.r0lo;
     r.r0hi = old.r0hi;
     r.r1lo = old.r1lo;
@@ -381,49 +420,61 @@ __host__ __device__ PairRec setup_pair(int a, int b, int n_views, const ViewRec*
     r.nk = old.nk;
     ok = old.status == 0;
   } else if (ok) {
-    // (scalars and selects only: no dynamically indexed local arrays here)
-    double cla[2], clb[2];
-    const double lena = view_arc(r.A[0], W, H, cla);
-    const double lenb = view_arc(r.A[1], W, H, clb);
+    df cla[2], clb[2];
+    const df lena = view_arc(Ad[0], W, H, cla);
+    const df lenb = view_arc(Ad[1], W, H, clb);
     // sample the shorter arc; ties (equal in exact arithmetic for mirror-symmetric
     // pairs) go to view a within a relative tolerance, not by rounding
-    const bool samp_a = lena <= lenb + 1e-9 * fmax(lena, lenb);
-    const double len_s = samp_a ? lena : lenb, len_o = samp_a ? lenb : lena;
-    const double csx = samp_a ? cla[0] : clb[0], csy = samp_a ? cla[1] : clb[1];
-    const double cox = samp_a ? clb[0] : cla[0], coy = samp_a ? clb[1] : cla[1];
-    const double dk = len_s / K;
-    r.dk = dk;
-    // one FP64 sincos: the rotations by dk, 16 dk and 32 dk follow by angle doubling
-    // (the angle error doubles with each step: about 1e-14 rad after six)
-    double sh, ch;
-    sincos(0.5 * dk, &sh, &ch);
-    auto twice = [](double& s_, double& c_) {
-      const double s2 = 2.0 * s_ * c_;
-      c_ = fma(c_, c_, -s_ * s_);
+    const bool samp_a = df_sub(lena, lenb).hi <= 1e-9f * fmaxf(lena.hi, lenb.hi);
+    const df len_s = samp_a ? lena : lenb, len_o = samp_a ? lenb : lena;
+    const df csx = samp_a ? cla[0] : clb[0], csy = samp_a ? cla[1] : clb[1];
+    const df cox = samp_a ? clb[0] : cla[0], coy = samp_a ? clb[1] : cla[1];
+    const df dk = df_div_f(len_s, (float)K);
+    r.dk = df_to_double(dk);
+    r.dk_hi = dk.hi;
+    r.dk_lo = dk.lo;
+    // one sincos: the rotations by dk, 16 dk and 32 dk follow by angle doubling (the
+    // angle error doubles with each step: about 1e-13 rad after six)
+    df sh, ch;
+    df_sincos(df_mul_f(dk, 0.5f), &sh, &ch);
+    auto twice = [](df& s_, df& c_) {
+      const df s2 = df_mul_f(df_mul(s_, c_), 2.0f);
+      c_ = df_sub(df_mul(c_, c_), df_mul(s_, s_));
       s_ = s2;
     };
-    r.c0[0] = ch * csx - sh * csy;
-    r.c0[1] = sh * csx + ch * csy;
-    double srot = sh, crot = ch;
-    twice(srot, crot);  // dk
-    r.rot[0] = crot;
-    r.rot[1] = srot;
+    auto rotate = [](df c, df s, df x, df y, df* ox, df* oy) {
+      *ox = df_sub(df_mul(c, x), df_mul(s, y));
+      *oy = df_add(df_mul(s, x), df_mul(c, y));
+    };
+    {
+      df c0x, c0y;
+      rotate(ch, sh, csx, csy, &c0x, &c0y);
+      r.c0[0] = df_to_double(c0x);
+      r.c0[1] = df_to_double(c0y);
+    }
     // valid samples of the other view: y_k = delta0 + (k + 1/2) dk, valid iff
     // y_k <= len_o or pi <= y_k <= pi + len_o (angles mod pi from its arc start)
-    if (len_o >= kPi) {
+    const df pi = df_pi();
+    if (!df_lt0(df_sub(len_o, pi))) {
       r.r0lo = 0;
       r.r0hi = K;
       r.r1lo = r.r1hi = K;
-    } else if (dk > 0.0) {
-      double d0 = atan2(cox * csy - coy * csx, cox * csx + coy * csy);
-      if (d0 < 0.0) d0 += kPi;
-      if (d0 >= kPi) d0 -= kPi;
-      const double e0 = floor((len_o - d0) / dk - 0.5);
-      const double s1 = ceil((kPi - d0) / dk - 0.5);
-      const double e1 = floor((kPi + len_o - d0) / dk - 0.5);
-      const int hi0 = (int)fmin(fmax(e0 + 1.0, 0.0), (double)K);
-      const int lo1 = (int)fmin(fmax(s1, (double)hi0), (double)K);
-      const int hi1 = (int)fmin(fmax(e1 + 1.0, (double)lo1), (double)K);
+    } else if (dk.hi > 0.0f) {
+      df d0 = df_atan2(df_cross2(cox, coy, csx, csy), df_add(df_mul(cox, csx), df_mul(coy, csy)));
+      if (df_lt0(d0)) d0 = df_add(d0, pi);
+      if (!df_lt0(df_sub(d0, pi))) d0 = df_sub(d0, pi);
+      const df idk = df_recip(dk);
+      const df half = {0.5f, 0.0f};
+      // floor / ceil of the sample positions (integer-valued FP32; K is exact in FP32)
+      float fr;
+      const float e0 = df_floor_frac(df_sub(df_mul(df_sub(len_o, d0), idk), half), &fr);
+      float s1 = df_floor_frac(df_sub(df_mul(df_sub(pi, d0), idk), half), &fr);
+      if (fr > 0.0f) s1 += 1.0f;
+      const float e1 = df_floor_frac(df_sub(df_mul(df_sub(df_add(pi, len_o), d0), idk), half), &fr);
+      const float Kf = (float)K;
+      const int hi0 = (int)fminf(fmaxf(e0 + 1.0f, 0.0f), Kf);
+      const int lo1 = (int)fminf(fmaxf(s1, (float)hi0), Kf);
+      const int hi1 = (int)fminf(fmaxf(e1 + 1.0f, (float)lo1), Kf);
       r.r0lo = 0;
       r.r0hi = hi0;
       r.r1lo = lo1;
@@ -432,40 +483,29 @@ __host__ __device__ PairRec setup_pair(int a, int b, int n_views, const ViewRec*
     r.nk = (r.r0hi - r.r0lo) + (r.r1hi - r.r1lo);
     // directions of the tile centres: tile t holds samples [32t, min(32t + 32, K)),
     // centred at ((k_begin + k_end) / 2) dk from the arc start; full tiles step by 32 dk
-    double s16 = srot, c16 = crot;
-    for (int i = 0; i < 4; ++i) twice(s16, c16);  // 16 dk
-    double s32 = s16, c32 = c16;
+    df s16 = sh, c16 = ch;
+    for (int i = 0; i < 5; ++i) twice(s16, c16);  // 16 dk
+    df s32 = s16, c32 = c16;
     twice(s32, c32);  // 32 dk
-    // full tiles step by 32 dk: the rotation runs in double-float on the FP32 pipes
-    // (about 1e-13 rad per step; FP64 is issued at 1/64 of the FP32 rate)
-    df cx0 = df_from_double(c16 * csx - s16 * csy);
-    df cy0 = df_from_double(s16 * csx + c16 * csy);
-    const df c32d = df_from_double(c32), s32d = df_from_double(s32);
+    df cx0, cy0;
+    rotate(c16, s16, csx, csy, &cx0, &cy0);
     float4* ct = ctile;
     for (int t = 0; t < n_tiles; ++t) {
       if (32 * t + 32 <= K) {
         ct[t] = make_float4(cx0.hi, cy0.hi, cx0.lo, cy0.lo);
       } else {  // last, partial tile
-        double sp, cp;
-        sincos(0.5 * (32.0 * t + K) * dk, &sp, &cp);
-        ct[t] = split_dir(cp * csx - sp * csy, sp * csx + cp * csy);
+        df sp, cp, px, py;
+        df_sincos(df_mul_f(dk, 0.5f * (float)(32 * t + K)), &sp, &cp);
+        rotate(cp, sp, csx, csy, &px, &py);
+        ct[t] = make_float4(px.hi, py.hi, px.lo, py.lo);
       }
-      const df nx = df_sub(df_mul(c32d, cx0), df_mul(s32d, cy0));
-      const df ny = df_add(df_mul(s32d, cx0), df_mul(c32d, cy0));
+      df nx, ny;
+      rotate(c32, s32, cx0, cy0, &nx, &ny);
       cx0 = nx;
       cy0 = ny;
     }
   }
   if (!ok) r.status = 1;
-  // double-float copies for the pair kernel
-  for (int s = 0; s < 2; ++s)
-    for (int i = 0; i < 6; ++i) {
-      const float h = (float)r.A[s][i];
-      r.Af[s][2 * i] = h;
-      r.Af[s][2 * i + 1] = (float)(r.A[s][i] - (double)h);
-    }
-  r.dk_hi = (float)r.dk;
-  r.dk_lo = (float)(r.dk - (double)r.dk_hi);
   return r;
 }
 
@@ -785,7 +825,7 @@ extern "C" int ecc_internal_setup_pair_host(int n_views, const double* P, const 
   info_out[5] = r.r0hi;
   info_out[6] = r.r1lo;
   info_out[7] = r.r1hi;
-  for (int i = 0; i < 12; ++i) A_out[i] = (&r.A[0][0])[i];
+  for (int i = 0; i < 12; ++i) A_out[i] = (double)(&r.Af[0][0])[2 * i] + (double)(&r.Af[0][0])[2 * i + 1];
   return 0;
 }
 

@@ -80,3 +80,26 @@ def test_host_setup_degenerate_pair():
     P = np.stack([sc["P"][0], 3.0 * sc["P"][0]]).reshape(-1, 12)
     info, _ = _setup(P, None, cfg.W, cfg.H, cfg.K, 0, 1)
     assert info[4] == 1 and info[3] == 0
+
+
+@pytest.mark.parametrize("name,stride,n_pairs,seed", [("c2", 4, 400, 5), ("c3", 2, 300, 6), ("c4", 10, 400, 7)])
+def test_host_setup_many_pairs(name, stride, n_pairs, seed):
+    """Seeded random pairs of the scan: the sampled arc, step and valid-sample set of
+    the (double-float) set-up against the oracle's FP64 arcs, pair by pair."""
+    cfg = synth.CONFIGS[name]
+    views = np.arange(0, cfg.n_views, stride)
+    sc = synth.make_scan(cfg, with_images=False, views=views)
+    P = sc["P"].reshape(-1, 12)
+    th = sc["motion"] if cfg.motion_rot_deg > 0 else None
+    rng = np.random.default_rng(seed)
+    n = len(views)
+    K = cfg.K
+    for _ in range(n_pairs):
+        a, b = (int(x) for x in rng.choice(n, 2, replace=False))
+        info, _ = _setup(P, th, cfg.W, cfg.H, K, a, b)
+        arcs = orc.pair_arcs(P[a], P[b], cfg.W, cfg.H, None if th is None else th[a], None if th is None else th[b])
+        assert info[4] == 0
+        assert np.isclose(info[2], arcs[2] / K, rtol=1e-12)
+        kap = arcs[1] + (np.arange(K) + 0.5) * arcs[2] / K
+        want = np.mod(kap - arcs[3], np.pi) <= arcs[4]
+        assert np.array_equal(_valid_set(info, K), want), (a, b)
