@@ -278,8 +278,8 @@ int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion,
   }
   if (grad) {
     hk.on_begin("view_tangent_kernel", s);
-    ecc::view_tangent_kernel<<<(n_views + 63) / 64, 64, 0, s>>>(n_views, P, motion, W, H,
-                                                               (ecc::ViewTan*)c->vtan.p);
+    ecc::view_tangent_kernel<<<(6 * n_views + 95) / 96, 96, 0, s>>>(n_views, P, motion, W, H,
+                                                                   (ecc::ViewTan*)c->vtan.p);
     hk.on_end("view_tangent_kernel", s);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "view tangent launch");
     hk.on_begin("view_grad_theta_kernel", s);

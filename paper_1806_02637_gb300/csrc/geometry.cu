@@ -222,11 +222,28 @@ __device__ ViewTan view_tangent(const double* P, const double* motion, int W, in
   return t;
 }
 
+// The same tangents, one thread per (view, motion parameter j): column j of the
+// view's ViewTan (a single tangent direction, six times the threads of one Dual<6>
+// per view).
 __global__ void view_tangent_kernel(int n_views, const double* __restrict__ P, const double* __restrict__ motion,
                                     int W, int H, ViewTan* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_views) return;
-  out[i] = view_tangent(P + 12 * i, motion ? motion + 6 * i : nullptr, W, H);
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 6LL * n_views) return;
+  const int lam = (int)(i / 6), j = (int)(i % 6);
+  using D1 = Dual<1>;
+  D1 th[6];
+  for (int k = 0; k < 6; ++k) th[k] = D1(motion ? motion[6 * lam + k] : 0.0);
+  th[j].d[0] = 1.0;
+  D1 Pm[12], Pn[12], C[3], up[3], cofc[9], u0, v0, D;
+  moved_projection(P + 12 * lam, th, Pm);
+  // a degenerate view's pairs carry no gradient; zero tangents keep its row at 0
+  const bool ok = view_geometry(Pm, W, H, Pn, C, up, cofc, &u0, &v0, &D);
+  ViewTan& t = out[lam];
+  for (int k = 0; k < 3; ++k) {
+    t.dC[k][j] = ok ? C[k].d[0] : 0.0;
+    t.dup[k][j] = ok ? up[k].d[0] : 0.0;
+  }
+  for (int k = 0; k < 9; ++k) t.dcofc[k][j] = ok ? cofc[k].d[0] : 0.0;
 }
 
 // Tangents of q = (C, up, cofc) with respect to the 12 entries of the unmoved P
