@@ -858,3 +858,21 @@ extern "C" int ecc_internal_akima_host(const double* y, int n, double h, double 
   *base = a.base;
   return 0;
 }
+
+// Internal host entry point (tests only): the double-float angle functions of the
+// per-pair set-up on the CPU.  op 0: out[2i], out[2i + 1] = sin, cos of x[i] (|x| <= 4);
+// op 1: out[i] = atan2(x[i], y[i]).  Inputs are split into double-float pairs first.
+extern "C" int ecc_internal_df_math_host(int op, const double* x, const double* y, int n, double* out) {
+  if (!x || !out || n < 0 || (op == 1 && !y) || op < 0 || op > 1) return -1;
+  for (int i = 0; i < n; ++i) {
+    if (op == 0) {
+      ecc::df s, c;
+      ecc::df_sincos(ecc::df_from_double(x[i]), &s, &c);
+      out[2 * i] = ecc::df_to_double(s);
+      out[2 * i + 1] = ecc::df_to_double(c);
+    } else {
+      out[i] = ecc::df_to_double(ecc::df_atan2(ecc::df_from_double(x[i]), ecc::df_from_double(y[i])));
+    }
+  }
+  return 0;
+}
