@@ -775,8 +775,8 @@ def run_ours(args):
                      "pair_kernel_frac_of_hbm": gbs / peaks.get("hbm_gbs", 6800.0),
                      # one ncu capture of this launch (one-pass metrics, same kernel build):
                      # DRAM read + write and L2 sector bytes per launch
-                     "pair_kernel_dram_bytes_ncu": 455751680 + 33869824,
-                     "pair_kernel_l2_bytes_ncu": 87438933 * 32}
+                     "pair_kernel_dram_bytes_ncu": 441123328 + 33391104,
+                     "pair_kernel_l2_bytes_ncu": 86831338 * 32}
     l2 = l2_read_rate(dev)
     if eval_only:
         eval_only["pair_kernel_frac_of_l2"] = eval_only["pair_kernel_gather_gbs"] / l2["gbs"]
@@ -796,7 +796,7 @@ def run_ours(args):
                           f"and the ECC of all {cfg.n_pairs} pairs ({t_ecc:.2f} s), FP64 on {cores} host threads")}
         E_or = oracle_energies(orc, scan["P"], S_or, cfg.W, cfg.H, cfg.K, r_or["pairs"])
         del S_or
-        oracle = {"d": r_or["d"], "total": r_or["total"], "E": E_or}
+        oracle = {"d": r_or["d"], "total": r_or["total"], "E": E_or, "nk": r_or["nk"]}
     accuracy = None
     if oracle is not None:
         r32 = ecc.ecc_evaluate(ctx, P, sino, cfg.W, cfg.H, cfg.K)

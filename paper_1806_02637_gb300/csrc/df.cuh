@@ -148,8 +148,10 @@ __host__ __device__ __forceinline__ df df_cos_poly(df x) {
 
 // sin and cos of a double-float angle |a| <= 4: a = q pi/2 + r with |r| <= pi/4 (q an
 // integer, r in double-float), Taylor series of sin r to r^17 and of cos r to r^18
-// (truncation below 1e-16 at |r| = pi/4), then the quadrant.
-__host__ __device__ inline void df_sincos(df a, df* s, df* c) {
+// (truncation below 1e-16 at |r| = pi/4), then the quadrant.  Not inlined: one copy of
+// the series serves every call (a kernel that inlined five copies waited on
+// instruction fetch).
+__host__ __device__ inline __noinline__ void df_sincos(df a, df* s, df* c) {
   const float q = rintf(a.hi * kDf2OverPi);
   const df qp = df_add(df_add(df_two_prod(q, kDfPio2A), df_two_prod(q, kDfPio2B)), df{q * kDfPio2C, 0.0f});
   const df r = df_sub(a, qp);
@@ -163,7 +165,7 @@ __host__ __device__ inline void df_sincos(df a, df* s, df* c) {
 // atan2(y, x) in double-float: the FP32 angle t0 and its sin and cos, then the
 // remaining turn d = atan((y cos t0 - x sin t0) / (x cos t0 + y sin t0)); |d| is a few
 // 1e-7, so d itself (error d^3 / 3) completes it.  atan2(0, 0) = 0.
-__host__ __device__ inline df df_atan2(df y, df x) {
+__host__ __device__ inline __noinline__ df df_atan2(df y, df x) {
   if (y.hi == 0.0f && x.hi == 0.0f) return df{0.0f, 0.0f};
   const float t0 = atan2f(y.hi, x.hi);
   df s0, c0;

@@ -327,7 +327,7 @@ __host__ __device__ bool pencil_frame_df(const ViewRec& va, const ViewRec& vb, d
 // over the angle between the extreme g's; otherwise every plane is valid.  The
 // corner values, the sign tests (each cross product once, with its antisymmetry for
 // the reversed order) and the angle run in double-float.
-__host__ __device__ df view_arc(const df* A, int W, int H, df* clo) {
+__host__ __device__ __noinline__ df view_arc(const df* A, int W, int H, df* clo) {
   const float hw = 0.5f * (float)W, hh = 0.5f * (float)H;  // exact
   const float xs[4] = {-hw, hw, hw, -hw};
   const float ys[4] = {-hh, -hh, hh, hh};
