@@ -408,7 +408,7 @@ def run_reference(args):
     job_s = per_view * cfg.n_views + per_pair * cfg.n_pairs
     value = cfg.n_pairs * cfg.K / job_s
     sample = (f"per step: dRadon/ds of {nv_step} of the {cfg.n_views} views (a different {nv_step} each step) and the "
-              f"ECC of the {len(pairs)} pairs among every {args.ref_stride}th view, on {cores} host threads; measured "
+              f"ECC of the {len(pairs)} pairs among one view in {args.ref_stride}, on {cores} host threads; measured "
               f"{per_view:.3f} s per view and {per_pair * 1e3:.4f} ms per pair over {args.steps} steps "
               f"({t_radon:.2f} s + {t_ecc:.2f} s), extrapolated to the whole job ({job_s:.1f} s)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
