@@ -154,9 +154,10 @@ int ecc_precompute_radon_derivative(ecc_ctx* ctx, int n_views, const double* P, 
  *   total    device FP64 [1]
  *   per_pair device FP64 [n_pairs][2] = {d, e} or NULL
  *   nkappa   device int32 [n_pairs] or NULL
- * Arithmetic: geometry per view and per pair in FP64; one line anchor per tile
- * of 64 samples (of 32 when n_kappa < 96) and view in double-float (about 48
- * bits); per-sample line offsets, interpolation and accumulation in FP32.
+ * Arithmetic: geometry per view in FP64; per pair (frame, maps, arcs, sample
+ * ranges) and one line anchor per tile of 64 samples (of 32 when n_kappa < 96)
+ * and view in double-float (about 48 bits); per-sample line offsets,
+ * interpolation and accumulation in FP32.
  * Limits: 1 <= n_kappa <= 65536; 0 <= n_pairs <= 2^31 - 1.
  */
 int ecc_evaluate(ecc_ctx* ctx, int n_views, const double* P, const double* motion, const void* sino,
