@@ -12,7 +12,6 @@
 
 namespace ecc {
 
-constexpr double kPi = 3.14159265358979323846;
 
 // Per-view set-up (FP64).  P is scaled so that the third row of M has unit norm
 // and det M > 0 (orientation-free: l = cof(M) n is invariant to P -> sP).

@@ -379,10 +379,11 @@ __host__ __device__ __noinline__ df view_arc(const df* A, int W, int H, df* clo)
 // Per-pair set-up: frame, kappa -> line maps, valid arcs, the sampled arc, the
 // integer ranges of valid samples and the tile-centre directions (ctile, n_tiles
 // entries).  With previous != NULL the sampling of *previous is kept and only the maps
-// follow the geometry.  GB300 issues FP64 at 1/64 of the FP32 rate, so the vector
-// algebra (frame, maps, corner values) runs in double-float on the FP32 pipes from the
-// views' double-float copies; the angles (atan2, sincos), the step and the integer
-// ranges stay in FP64.
+// follow the geometry.  GB300 issues FP64 at 1/64 of the FP32 rate, so everything
+// here runs in double-float (about 48 bits) on the FP32 pipes from the views'
+// double-float copies: the frame, the maps, the corner values and signs, the angles
+// (df_atan2, df_sincos), the step and the positions whose floors give the integer
+// ranges.
 __host__ __device__ PairRec setup_pair(int a, int b, int n_views, const ViewRec* views, int W, int H, int K,
                                        float4* ctile, int n_tiles, const PairRec* previous) {
   const bool reuse_sampling = previous != nullptr;
