@@ -231,7 +231,7 @@ int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion,
     if ((rc = ensure(c, c->Gpp, sizeof(double) * 12 * (size_t)np, "pair adjoints")) != ECC_OK) return rc;
   }
   if (grad || grad_P) {
-    if ((rc = ensure(c, c->gq, sizeof(double) * 30 * (size_t)np, "pair q gradients")) != ECC_OK) return rc;
+    if ((rc = ensure(c, c->gq, sizeof(float2) * 30 * (size_t)np, "pair q gradients")) != ECC_OK) return rc;
   }
   if (grad) {
     if ((rc = ensure(c, c->vtan, sizeof(ecc::ViewTan) * (size_t)n_views, "view tangents")) != ECC_OK) return rc;
@@ -272,7 +272,7 @@ int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion,
     hk.on_begin("pair_grad_q_kernel", s);
     ecc::pair_grad_q_kernel<<<(unsigned)((np + 63) / 64), 64, 0, s>>>(np, (const ecc::PairRec*)c->pairs.p,
                                                                       (const ecc::ViewRec*)c->views.p,
-                                                                      (const double*)c->Gpp.p, (double*)c->gq.p);
+                                                                      (const double*)c->Gpp.p, (float2*)c->gq.p);
     hk.on_end("pair_grad_q_kernel", s);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "pair q gradient launch");
   }
@@ -283,7 +283,7 @@ int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion,
     hk.on_end("view_tangent_kernel", s);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "view tangent launch");
     hk.on_begin("view_grad_theta_kernel", s);
-    ecc::view_grad_theta_kernel<<<n_views, 256, 0, s>>>(n_views, np, pairs, (const double*)c->gq.p,
+    ecc::view_grad_theta_kernel<<<n_views, 256, 0, s>>>(n_views, np, pairs, (const float2*)c->gq.p,
                                                         (const ecc::ViewTan*)c->vtan.p, grad);
     hk.on_end("view_grad_theta_kernel", s);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "gradient reduce launch");
@@ -295,7 +295,7 @@ int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion,
     hk.on_end("view_tangent_P_kernel", s);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "view P tangent launch");
     hk.on_begin("view_grad_P_kernel", s);
-    ecc::view_grad_P_kernel<<<n_views, 256, 0, s>>>(n_views, np, pairs, (const double*)c->gq.p,
+    ecc::view_grad_P_kernel<<<n_views, 256, 0, s>>>(n_views, np, pairs, (const float2*)c->gq.p,
                                                     (const ecc::ViewTanP*)c->vtanP.p, grad_P);
     hk.on_end("view_grad_P_kernel", s);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "P gradient reduce launch");

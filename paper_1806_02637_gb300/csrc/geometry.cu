@@ -106,67 +106,6 @@ __host__ __device__ bool view_geometry(const T* Pm, int W, int H, T* Pn, T* C, T
   return ok;
 }
 
-// Reverse mode of the pencil frame (FP64; the frame that pencil_frame_df builds):
-// given gw = d e / d w and gv = d e / d v, adds d e / d (Ca, Cb, upa, upb) to gCa, gCb
-// and gup (the same for both up axes, which enter as their sum); also returns w and v.  Each step's adjoint follows from its
-// forward rule: v = w x u gives w' += u x v', u' += v' x w; y = x / |x| gives
-// x' = (y' - (y'.y) y) / |x|; w_t = r - (r.u) u gives r' = w_t' - (w_t'.u) u and
-// u' -= (w_t'.u) r + (r.u) w_t' (for the fallback axis e: u' -= (w_t'.u) e_ax + u_ax w_t').
-__host__ __device__ bool pencil_frame_adjoint(const double* Ca, const double* Cb, const double* upa,
-                                              const double* upb, const double* gw, const double* gv,
-                                              double* w, double* v, double* gCa, double* gCb, double* gup) {
-  double d[3] = {Cb[0] - Ca[0], Cb[1] - Ca[1], Cb[2] - Ca[2]};
-  const double nd = sqrt(dot3(d, d));
-  if (!(nd > 0.0)) return false;
-  double u[3];
-  for (int k = 0; k < 3; ++k) u[k] = d[k] / nd;
-  double rr[3] = {upa[0] + upb[0], upa[1] + upb[1], upa[2] + upb[2]};
-  const double ru = dot3(rr, u);
-  double wt[3];
-  for (int k = 0; k < 3; ++k) wt[k] = rr[k] - ru * u[k];
-  double nw = sqrt(dot3(wt, wt));
-  int ax = -1;
-  if (nw < 1e-6) {
-    const double best = fmin(fabs(u[0]), fmin(fabs(u[1]), fabs(u[2])));
-    ax = 0;
-    while (fabs(u[ax]) > best + 1e-9) ++ax;
-    const double ui = u[ax];
-    for (int k = 0; k < 3; ++k) wt[k] = (k == ax ? 1.0 : 0.0) - ui * u[k];
-    nw = sqrt(dot3(wt, wt));
-  }
-  for (int k = 0; k < 3; ++k) w[k] = wt[k] / nw;
-  cross3(w, u, v);
-  // reverse
-  double gwt_in[3], gu[3], tmp[3];
-  cross3(u, gv, tmp);  // d e / d w from v = w x u
-  for (int k = 0; k < 3; ++k) gwt_in[k] = gw[k] + tmp[k];
-  cross3(gv, w, gu);   // d e / d u from v = w x u
-  const double gww = dot3(gwt_in, w);
-  double gwt[3];
-  for (int k = 0; k < 3; ++k) gwt[k] = (gwt_in[k] - gww * w[k]) / nw;
-  const double gwu = dot3(gwt, u);
-  if (ax < 0) {
-    for (int k = 0; k < 3; ++k) {
-      gup[k] = gwt[k] - gwu * u[k];
-      gu[k] -= gwu * rr[k] + ru * gwt[k];
-    }
-  } else {
-    const double ui = u[ax];
-    for (int k = 0; k < 3; ++k) {
-      gup[k] = 0.0;
-      gu[k] -= ui * gwt[k];
-    }
-    gu[ax] -= gwu;
-  }
-  const double guu = dot3(gu, u);
-  for (int k = 0; k < 3; ++k) {
-    const double gd = (gu[k] - guu * u[k]) / nd;
-    gCb[k] = gd;
-    gCa[k] = -gd;
-  }
-  return true;
-}
-
 }  // namespace
 
 __host__ __device__ ViewRec setup_view(const double* P, const double* motion, int W, int H) {
@@ -317,6 +256,73 @@ __host__ __device__ bool pencil_frame_df(const ViewRec& va, const ViewRec& vb, d
   v[0] = df_cross2(w[1], w[2], u[1], u[2]);
   v[1] = df_cross2(w[2], w[0], u[2], u[0]);
   v[2] = df_cross2(w[0], w[1], u[0], u[1]);
+  return true;
+}
+
+// Reverse mode of pencil_frame_df (the same steps in double-float): given gw = d e / d w
+// and gv = d e / d v, returns d e / d (Ca, Cb, up) in gCa, gCb and gup (the same for both
+// up axes, which enter as their sum).  Each step's adjoint follows from its forward
+// rule: v = w x u gives w' += u x v', u' += v' x w; y = x / |x| gives
+// x' = (y' - (y'.y) y) / |x|; w_t = r - (r.u) u gives r' = w_t' - (w_t'.u) u and
+// u' -= (w_t'.u) r + (r.u) w_t' (for the fallback axis e: u' -= (w_t'.u) e_ax + u_ax w_t').
+__host__ __device__ bool pencil_frame_adjoint_df(const ViewRec& va, const ViewRec& vb, const df* gw, const df* gv,
+                                                 df* w, df* v, df* gCa, df* gCb, df* gup) {
+  df d[3], rr[3], u[3], wt[3];
+  for (int k = 0; k < 3; ++k) {
+    d[k] = df_sub(qget(vb, k), qget(va, k));
+    rr[k] = df_add(qget(va, 3 + k), qget(vb, 3 + k));
+  }
+  const df nd2 = df_dot3(d, d);
+  if (!(nd2.hi > 0.0f)) return false;
+  const df ind = df_rsqrt(nd2);
+  for (int k = 0; k < 3; ++k) u[k] = df_mul(d[k], ind);
+  const df ru = df_dot3(rr, u);
+  for (int k = 0; k < 3; ++k) wt[k] = df_sub(rr[k], df_mul(ru, u[k]));
+  df nw2 = df_dot3(wt, wt);
+  int ax = -1;
+  if (nw2.hi < 1e-12f) {
+    const double ua[3] = {fabs(df_to_double(u[0])), fabs(df_to_double(u[1])), fabs(df_to_double(u[2]))};
+    const double best = fmin(ua[0], fmin(ua[1], ua[2]));
+    ax = ua[0] <= best + 1e-9 ? 0 : (ua[1] <= best + 1e-9 ? 1 : 2);
+    const df ui = ax == 0 ? u[0] : (ax == 1 ? u[1] : u[2]);
+    for (int k = 0; k < 3; ++k) wt[k] = df_sub(df{k == ax ? 1.0f : 0.0f, 0.0f}, df_mul(ui, u[k]));
+    nw2 = df_dot3(wt, wt);
+  }
+  const df inw = df_rsqrt(nw2);
+  for (int k = 0; k < 3; ++k) w[k] = df_mul(wt[k], inw);
+  v[0] = df_cross2(w[1], w[2], u[1], u[2]);
+  v[1] = df_cross2(w[2], w[0], u[2], u[0]);
+  v[2] = df_cross2(w[0], w[1], u[0], u[1]);
+  // reverse
+  df gwt_in[3], gu[3], gwt[3];
+  gwt_in[0] = df_add(gw[0], df_cross2(u[1], u[2], gv[1], gv[2]));  // d e / d w from v = w x u
+  gwt_in[1] = df_add(gw[1], df_cross2(u[2], u[0], gv[2], gv[0]));
+  gwt_in[2] = df_add(gw[2], df_cross2(u[0], u[1], gv[0], gv[1]));
+  gu[0] = df_cross2(gv[1], gv[2], w[1], w[2]);  // d e / d u from v = w x u
+  gu[1] = df_cross2(gv[2], gv[0], w[2], w[0]);
+  gu[2] = df_cross2(gv[0], gv[1], w[0], w[1]);
+  const df gww = df_dot3(gwt_in, w);
+  for (int k = 0; k < 3; ++k) gwt[k] = df_mul(df_sub(gwt_in[k], df_mul(gww, w[k])), inw);
+  const df gwu = df_dot3(gwt, u);
+  if (ax < 0) {
+    for (int k = 0; k < 3; ++k) {
+      gup[k] = df_sub(gwt[k], df_mul(gwu, u[k]));
+      gu[k] = df_sub(gu[k], df_add(df_mul(gwu, rr[k]), df_mul(ru, gwt[k])));
+    }
+  } else {
+    const df ui = ax == 0 ? u[0] : (ax == 1 ? u[1] : u[2]);
+    for (int k = 0; k < 3; ++k) {
+      gup[k] = df{0.0f, 0.0f};
+      gu[k] = df_sub(gu[k], df_mul(ui, gwt[k]));
+    }
+    gu[ax] = df_sub(gu[ax], gwu);
+  }
+  const df guu = df_dot3(gu, u);
+  for (int k = 0; k < 3; ++k) {
+    const df gd = df_mul(df_sub(gu[k], df_mul(guu, u[k])), ind);
+    gCb[k] = gd;
+    gCa[k] = df_neg(gd);
+  }
   return true;
 }
 
@@ -550,69 +556,77 @@ __global__ void pair_setup_kernel(int n_views, long long p_begin, long long p_en
 
 // Gradient of one pair's e with respect to the per-view quantities the pair reads,
 // q = (C[3], up[3], cofc[9]) of view a, then of view b (30 values), from
-// G = d e / d A (the pair kernel's adjoint): A = cofc [w v] is linear in cofc, and
-// the frame (w, v) is differentiated in reverse mode (pencil_frame_adjoint).
+// G = d e / d A (the pair kernel's adjoint, FP32 values): A = cofc [w v] is linear in
+// cofc, and the frame (w, v) is differentiated in reverse mode
+// (pencil_frame_adjoint_df).  Double-float throughout; out holds (hi, lo) pairs.
 __device__ void pair_grad_q(const PairRec& pr, const ViewRec* __restrict__ views, const double* __restrict__ G,
-                            double* __restrict__ out) {
+                            float2* __restrict__ out) {
   if (pr.status != 0 || pr.nk <= 0) {
-    for (int j = 0; j < 30; ++j) out[j] = 0.0;
+    for (int j = 0; j < 30; ++j) out[j] = make_float2(0.0f, 0.0f);
     return;
   }
   const ViewRec& va = views[pr.a];
   const ViewRec& vb = views[pr.b];
   const ViewRec* vv[2] = {&va, &vb};
+  df g[12];
+  for (int i = 0; i < 12; ++i) g[i] = df{(float)G[i], 0.0f};  // an FP32 value: exact
   // d e / d w and d e / d v through A = cofc [w v]
-  double gw[3] = {0.0, 0.0, 0.0}, gv[3] = {0.0, 0.0, 0.0};
+  df gw[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}}, gv[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
   for (int s = 0; s < 2; ++s)
     for (int i = 0; i < 3; ++i) {
-      const double g0 = G[6 * s + 2 * i], g1 = G[6 * s + 2 * i + 1];
-      const double* cof = vv[s]->cofc + 3 * i;
+      const df g0 = g[6 * s + 2 * i], g1 = g[6 * s + 2 * i + 1];
       for (int k = 0; k < 3; ++k) {
-        gw[k] += g0 * cof[k];
-        gv[k] += g1 * cof[k];
+        const df cof = qget(*vv[s], 6 + 3 * i + k);
+        gw[k] = df_add(gw[k], df_mul(g0, cof));
+        gv[k] = df_add(gv[k], df_mul(g1, cof));
       }
     }
-  double w[3], v[3], gCa[3], gCb[3], gup[3];
-  if (!pencil_frame_adjoint(va.C, vb.C, va.up, vb.up, gw, gv, w, v, gCa, gCb, gup)) {
-    for (int j = 0; j < 30; ++j) out[j] = 0.0;
+  df w[3], v[3], gCa[3], gCb[3], gup[3];
+  if (!pencil_frame_adjoint_df(va, vb, gw, gv, w, v, gCa, gCb, gup)) {
+    for (int j = 0; j < 30; ++j) out[j] = make_float2(0.0f, 0.0f);
     return;
   }
+  auto put = [&](int j, df x) { out[j] = make_float2(x.hi, x.lo); };
   for (int s = 0; s < 2; ++s)
     for (int i = 0; i < 3; ++i) {
-      const double g0 = G[6 * s + 2 * i], g1 = G[6 * s + 2 * i + 1];
-      for (int k = 0; k < 3; ++k) out[15 * s + 6 + 3 * i + k] = g0 * w[k] + g1 * v[k];
+      const df g0 = g[6 * s + 2 * i], g1 = g[6 * s + 2 * i + 1];
+      for (int k = 0; k < 3; ++k) put(15 * s + 6 + 3 * i + k, df_add(df_mul(g0, w[k]), df_mul(g1, v[k])));
     }
   for (int k = 0; k < 3; ++k) {
-    out[k] = gCa[k];
-    out[3 + k] = gup[k];
-    out[15 + k] = gCb[k];
-    out[18 + k] = gup[k];
+    put(k, gCa[k]);
+    put(3 + k, gup[k]);
+    put(15 + k, gCb[k]);
+    put(18 + k, gup[k]);
   }
 }
 
 __global__ void pair_grad_q_kernel(long long n_pairs, const PairRec* __restrict__ prs,
                                    const ViewRec* __restrict__ views, const double* __restrict__ Gpp,
-                                   double* __restrict__ gq) {
+                                   float2* __restrict__ gq) {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n_pairs) return;
   pair_grad_q(prs[p], views, Gpp + 12 * p, gq + 30 * p);
 }
 
 // Per-view sum of the pairs' q gradients in a fixed order (one block of 256 threads
-// per view): on return sh[k][0] (k < 15) holds d total / d q_k of view lam.  With
-// pairs == NULL the pairs of a view are found by the row-major a < b enumeration,
-// otherwise by scanning the pair list.
+// per view), in double-float: on return sh[k][0] (k < 15) holds d total / d q_k of view
+// lam as a (hi, lo) pair.  With pairs == NULL the pairs of a view are found by the
+// row-major a < b enumeration, otherwise by scanning the pair list.
 __device__ void reduce_q_block(int lam, int n_views, long long n_pairs, const int32_t* __restrict__ pairs,
-                               const double* __restrict__ gq, double (*sh)[256]) {
-  double acc[15];
-  for (int k = 0; k < 15; ++k) acc[k] = 0.0;
+                               const float2* __restrict__ gq, float2 (*sh)[256]) {
+  df acc[15];
+  for (int k = 0; k < 15; ++k) acc[k] = df{0.0f, 0.0f};
+  auto add = [&](const float2* q) {
+    for (int k = 0; k < 15; ++k) {
+      const float2 x = q[k];
+      acc[k] = df_add(acc[k], df{x.x, x.y});
+    }
+  };
   if (pairs) {
     for (long long p = threadIdx.x; p < n_pairs; p += blockDim.x) {
       const int a = pairs[2 * p], b = pairs[2 * p + 1];
-      if (a == lam)
-        for (int k = 0; k < 15; ++k) acc[k] += gq[30 * p + k];
-      if (b == lam)
-        for (int k = 0; k < 15; ++k) acc[k] += gq[30 * p + 15 + k];
+      if (a == lam) add(gq + 30 * p);
+      if (b == lam) add(gq + 30 * p + 15);
     }
   } else {
     const long long n = n_views;
@@ -621,35 +635,43 @@ __device__ void reduce_q_block(int lam, int n_views, long long n_pairs, const in
       const long long a = o < lam ? o : lam, b = o < lam ? lam : o;
       const long long p = a * (2 * n - a - 1) / 2 + (b - a - 1);
       const int off = o < lam ? 15 : 0;  // this view is b of the pair when o < lam
-      for (int k = 0; k < 15; ++k) acc[k] += gq[30 * p + off + k];
+      add(gq + 30 * p + off);
     }
   }
-  for (int k = 0; k < 15; ++k) sh[k][threadIdx.x] = acc[k];
+  for (int k = 0; k < 15; ++k) sh[k][threadIdx.x] = make_float2(acc[k].hi, acc[k].lo);
   __syncthreads();
   for (int wdt = blockDim.x / 2; wdt > 0; wdt >>= 1) {
     if (threadIdx.x < wdt)
-      for (int k = 0; k < 15; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + wdt];
+      for (int k = 0; k < 15; ++k) {
+        const float2 x = sh[k][threadIdx.x], y = sh[k][threadIdx.x + wdt];
+        const df z = df_add(df{x.x, x.y}, df{y.x, y.y});
+        sh[k][threadIdx.x] = make_float2(z.hi, z.lo);
+      }
     __syncthreads();
   }
 }
 
+__device__ __forceinline__ double sh_value(const float2 (*sh)[256], int k) {
+  return (double)sh[k][0].x + (double)sh[k][0].y;
+}
+
 // d total / d theta of one view from its q gradient (sh[k][0]) and the tangents
 // d q / d theta (C, up, cofc rows).
-__device__ __forceinline__ double contract_theta(const double (*sh)[256], const ViewTan& t, int j) {
+__device__ __forceinline__ double contract_theta(const float2 (*sh)[256], const ViewTan& t, int j) {
   double g = 0.0;
-  for (int k = 0; k < 3; ++k) g += sh[k][0] * t.dC[k][j];
-  for (int k = 0; k < 3; ++k) g += sh[3 + k][0] * t.dup[k][j];
-  for (int k = 0; k < 9; ++k) g += sh[6 + k][0] * t.dcofc[k][j];
+  for (int k = 0; k < 3; ++k) g += sh_value(sh, k) * t.dC[k][j];
+  for (int k = 0; k < 3; ++k) g += sh_value(sh, 3 + k) * t.dup[k][j];
+  for (int k = 0; k < 9; ++k) g += sh_value(sh, 6 + k) * t.dcofc[k][j];
   return g;
 }
 
 // grad[view][6] = d total / d theta (one block of 256 threads per view).
 __global__ void __launch_bounds__(256) view_grad_theta_kernel(int n_views, long long n_pairs,
                                                               const int32_t* __restrict__ pairs,
-                                                              const double* __restrict__ gq,
+                                                              const float2* __restrict__ gq,
                                                               const ViewTan* __restrict__ vtan,
                                                               double* __restrict__ grad) {
-  __shared__ double sh[15][256];
+  __shared__ float2 sh[15][256];
   const int lam = blockIdx.x;
   reduce_q_block(lam, n_views, n_pairs, pairs, gq, sh);
   if (threadIdx.x < 6) grad[6 * lam + threadIdx.x] = contract_theta(sh, vtan[lam], threadIdx.x);
@@ -658,16 +680,16 @@ __global__ void __launch_bounds__(256) view_grad_theta_kernel(int n_views, long 
 // grad_P[view][12] = d total / d P (one block of 256 threads per view).
 __global__ void __launch_bounds__(256) view_grad_P_kernel(int n_views, long long n_pairs,
                                                           const int32_t* __restrict__ pairs,
-                                                          const double* __restrict__ gq,
+                                                          const float2* __restrict__ gq,
                                                           const ViewTanP* __restrict__ vtan,
                                                           double* __restrict__ grad_P) {
-  __shared__ double sh[15][256];
+  __shared__ float2 sh[15][256];
   const int lam = blockIdx.x;
   reduce_q_block(lam, n_views, n_pairs, pairs, gq, sh);
   if (threadIdx.x < 12) {
     const ViewTanP& t = vtan[lam];
     double g = 0.0;
-    for (int k = 0; k < 15; ++k) g += sh[k][0] * t.d[k][threadIdx.x];
+    for (int k = 0; k < 15; ++k) g += sh_value(sh, k) * t.d[k][threadIdx.x];
     grad_P[12 * lam + threadIdx.x] = g;
   }
 }
@@ -714,7 +736,7 @@ __global__ void serve_pair_grad_kernel(const ServeJob* __restrict__ jobs, const 
 
 __global__ void __launch_bounds__(256) serve_view_grad_kernel(const ServeJob* __restrict__ jobs,
                                                               const long long* __restrict__ voff, int n_jobs) {
-  __shared__ double sh[15][256];
+  __shared__ float2 sh[15][256];
   const long long i = blockIdx.x;
   const int j = serve_job_of(voff, n_jobs, i);
   const ServeJob& J = jobs[j];
@@ -874,6 +896,39 @@ extern "C" int ecc_internal_df_math_host(int op, const double* x, const double* 
     } else {
       out[i] = ecc::df_to_double(ecc::df_atan2(ecc::df_from_double(x[i]), ecc::df_from_double(y[i])));
     }
+  }
+  return 0;
+}
+
+// Internal host entry point (tests only): the pencil frame of two sources and its
+// reverse mode (pencil_frame_df, pencil_frame_adjoint_df) on the CPU.
+//   Ca, Cb, upa, upb [3] host FP64; gw, gv [3] the incoming d e / d w, d e / d v
+//   w_v_out [6] = w, v; grad_out [9] = d e / d Ca, d e / d Cb, d e / d up (each up axis)
+// Returns -1 for coincident sources.
+extern "C" int ecc_internal_frame_adjoint_host(const double* Ca, const double* Cb, const double* upa,
+                                               const double* upb, const double* gw, const double* gv,
+                                               double* w_v_out, double* grad_out) {
+  ecc::ViewRec va{}, vb{};
+  for (int k = 0; k < 3; ++k) {
+    const ecc::df ca = ecc::df_from_double(Ca[k]), cb = ecc::df_from_double(Cb[k]);
+    const ecc::df ua = ecc::df_from_double(upa[k]), ub = ecc::df_from_double(upb[k]);
+    va.qdf[2 * k] = ca.hi; va.qdf[2 * k + 1] = ca.lo;
+    vb.qdf[2 * k] = cb.hi; vb.qdf[2 * k + 1] = cb.lo;
+    va.qdf[6 + 2 * k] = ua.hi; va.qdf[6 + 2 * k + 1] = ua.lo;
+    vb.qdf[6 + 2 * k] = ub.hi; vb.qdf[6 + 2 * k + 1] = ub.lo;
+  }
+  ecc::df g_w[3], g_v[3], w[3], v[3], gCa[3], gCb[3], gup[3];
+  for (int k = 0; k < 3; ++k) {
+    g_w[k] = ecc::df_from_double(gw[k]);
+    g_v[k] = ecc::df_from_double(gv[k]);
+  }
+  if (!ecc::pencil_frame_adjoint_df(va, vb, g_w, g_v, w, v, gCa, gCb, gup)) return -1;
+  for (int k = 0; k < 3; ++k) {
+    w_v_out[k] = ecc::df_to_double(w[k]);
+    w_v_out[3 + k] = ecc::df_to_double(v[k]);
+    grad_out[k] = ecc::df_to_double(gCa[k]);
+    grad_out[3 + k] = ecc::df_to_double(gCb[k]);
+    grad_out[6 + k] = ecc::df_to_double(gup[k]);
   }
   return 0;
 }

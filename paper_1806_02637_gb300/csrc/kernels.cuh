@@ -14,13 +14,13 @@ __global__ void pair_setup_kernel(int n_views, long long p_begin, long long p_en
                                   const ViewRec* views, int W, int H, int K, PairRec* out, float4* ctile, int n_tiles,
                                   int reuse_sampling, int* status);
 __global__ void view_tangent_kernel(int n_views, const double* P, const double* motion, int W, int H, ViewTan* out);
-__global__ void view_grad_theta_kernel(int n_views, long long n_pairs, const int32_t* pairs, const double* gq,
+__global__ void view_grad_theta_kernel(int n_views, long long n_pairs, const int32_t* pairs, const float2* gq,
                                        const ViewTan* vtan, double* grad);
 __global__ void view_tangent_P_kernel(int n_views, const double* P, const double* motion, int W, int H,
                                       ViewTanP* out);
 __global__ void pair_grad_q_kernel(long long n_pairs, const PairRec* prs, const ViewRec* views, const double* Gpp,
-                                   double* gq);
-__global__ void view_grad_P_kernel(int n_views, long long n_pairs, const int32_t* pairs, const double* gq,
+                                   float2* gq);
+__global__ void view_grad_P_kernel(int n_views, long long n_pairs, const int32_t* pairs, const float2* gq,
                                    const ViewTanP* vtan, double* grad_P);
 __global__ void alpha_dir_kernel(int n_alpha, float4* dir);
 
@@ -124,7 +124,7 @@ struct ServeJob {
   double* grad;      // [n_views][6]
   ViewRec* views;
   ViewTan* vtan;
-  double* gpp;        // [n_pairs][30] d e / d (C, up, cofc) of views a and b
+  float2* gpp;        // [n_pairs][30] d e / d (C, up, cofc) of views a and b, double-float pairs
   double* total_out;  // this round's total
   int* status;
   // motion model: per-view (theta stepped directly) or Akima spline of node values

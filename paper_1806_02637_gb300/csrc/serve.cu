@@ -81,7 +81,7 @@ Layout layout_of(const ecc_job& j) {
   L.ctile = take(np * n_tiles * sizeof(float4));
   L.partial = take((np + kWarpsPerPairBlock - 1) / kWarpsPerPairBlock * sizeof(double));
   L.Gpp = take(np * 12 * sizeof(double));
-  L.gpp = take(np * 30 * sizeof(double));
+  L.gpp = take(np * 30 * sizeof(float2));
   L.totals = take(((size_t)j.n_iters + 1) * sizeof(double));
   L.status = take(sizeof(int));
   L.theta0 = take(n * 6 * sizeof(double));
@@ -432,7 +432,7 @@ void round_loop(ecc_serve* S) {
       s.grad = (double*)(R + L.grad);
       s.views = (ecc::ViewRec*)(R + L.views);
       s.vtan = (ecc::ViewTan*)(R + L.vtan);
-      s.gpp = (double*)(R + L.gpp);
+      s.gpp = (float2*)(R + L.gpp);
       s.total_out = (double*)(R + L.totals) + J->rounds;
       s.status = (int*)(R + L.status);
       s.model = d.motion_model;
