@@ -44,6 +44,10 @@ struct ecc_ctx {
   Buf views, pairs, ctile, adir, perpair, nk, partial, rtable, wimg, stage;
   Buf vtan, Gpp, gq;  // adjoint scratch: view tangents (theta), d e / d A, d e / d (C, up, cofc)
   Buf vtanP;          // view tangents with respect to P
+  // the alpha-row direction table in adir was written for adir_n rows at adir_ptr
+  // (calls on one context share one stream, so a later call finds it complete)
+  int adir_n = 0;
+  const void* adir_ptr = nullptr;
   // sampling of the last evaluation (for ecc_evaluate_frozen)
   bool samp_valid = false;
   int samp_views = 0, samp_pairs = 0, samp_K = 0, samp_W = 0, samp_H = 0;
@@ -246,10 +250,14 @@ int run_evaluate(ecc_ctx* c, int n_views, const double* P, const double* motion,
                                                               c->d_status);
   hk.on_end("view_setup_kernel", s);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "view set-up launch");
-  hk.on_begin("alpha_dir_kernel", s);
-  ecc::alpha_dir_kernel<<<(n_alpha + 255) / 256, 256, 0, s>>>(n_alpha, (float4*)c->adir.p);
-  hk.on_end("alpha_dir_kernel", s);
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "alpha table launch");
+  if (c->adir_n != n_alpha || c->adir_ptr != c->adir.p) {  // the table depends on n_alpha only
+    hk.on_begin("alpha_dir_kernel", s);
+    ecc::alpha_dir_kernel<<<(n_alpha + 255) / 256, 256, 0, s>>>(n_alpha, (float4*)c->adir.p);
+    hk.on_end("alpha_dir_kernel", s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "alpha table launch");
+    c->adir_n = n_alpha;
+    c->adir_ptr = c->adir.p;
+  }
   // One pair set-up launch, then one pair-kernel launch, on the caller's stream.  (Set-up
   // chunks on a second stream beside the pair kernel's chunks were measured slower: the
   // two kernels sharing SMs slowed each other, 0.707 -> 0.765 ms on the 496-view scan.)
