@@ -3,8 +3,8 @@
 // Data layout in device memory
 //   P            [n_views][12]  FP64, row-major 3x4, world mm -> pixel homogeneous
 //   sinogram     [n_views][n_alpha][n_s]  FP32 (alpha-major, rows contiguous in s)
-//   ViewRec      [n_views]      FP64 per-view set-up (K0)
-//   PairRec      [n_pairs]      FP64/int per-pair set-up (pair set-up kernel)
+//   ViewRec      [n_views]      FP64 per-view set-up (K0), with double-float copies
+//   PairRec      [n_pairs]      double-float/int per-pair set-up (pair set-up kernel)
 //   per-pair out {d, e} FP64 + N_kappa int32
 #pragma once
 #include <cstdint>
@@ -41,7 +41,7 @@ struct ViewTanP {
   double d[15][12];
 };
 
-// Per-pair set-up (FP64 geometry, integer sample ranges).
+// Per-pair set-up (double-float maps, integer sample ranges).
 struct PairRec {
   float Af[2][12];  // per view (a, b): l_centred(kappa) = A (cos kappa, sin kappa), A 3x2 row-major,
                     // each entry a double-float pair (hi, lo)

@@ -1,5 +1,5 @@
 // Per-view and per-pair set-up of the ECC path (no matrix inverse anywhere): FP64 per
-// view, double-float vector algebra with FP64 angles per pair.
+// view, double-float (about 48 bits, on the FP32 pipes) per pair.
 //
 //  view_setup_kernel  one thread per view: rigid motion P' = P T(theta), scaling,
 //                     source as the meet of the rows of P (Eq. 4/5), cofactor
