@@ -281,6 +281,18 @@ def serving_leg(args, c2_scan):
         ref = float(ecc.ecc_evaluate(ctx, Pd, S, W, H, K, motion=torch.from_numpy(th).cuda(),
                                      want_per_pair=False)["total"].cpu()[0])
         acc.append(abs(results[j]["total_first"] - ref) / abs(ref))
+    # two jobs' first totals against the FP64 oracle (its own dRadon/ds of the job's views): the two
+    # with the least dRadon/ds work for the oracle (views x detector pixels)
+    from oracle import oracle as orc
+    acc_or = []
+    small_or = sorted(range(len(jobs)), key=lambda j: jobs[j][3].shape[0] * jobs[j][3].shape[1] * jobs[j][3].shape[2])[:2]
+    for j in small_or:
+        _, det, P, I, K, th = jobs[j]
+        W, H, _, na, ns, _ = SERVE_DETECTORS[det]
+        Pn = P.numpy().astype(np.float64)
+        S_or = orc.radon_derivative(Pn, I.numpy(), na, ns)
+        ref = orc.ecc(Pn, S_or, W, H, K, motion=th)["total"]
+        acc_or.append(abs(results[j]["total_first"] - ref) / abs(ref))
     # the same jobs, one after the other, through plain calls on one stream: upload,
     # precompute, n_iters x (ecc_evaluate_grad, step), final ecc_evaluate.  Two passes:
     # the first also pays one-time costs (first allocations of each job shape, first
@@ -323,6 +335,10 @@ def serving_leg(args, c2_scan):
                                              "launches)"},
             "max_jobs_per_round": st["max_batch"], "iterations_per_job": iters, "step": step,
             "fp16_vs_fp32_total_rel_err": {"jobs": len(acc), "max": float(max(acc)) if acc else None},
+            "fp16_vs_oracle_total_rel_err": {"jobs": len(acc_or), "max": float(max(acc_or)) if acc_or else None,
+                                             "how": "first totals (at the initial motion) of the two jobs with the "
+                                                    "fewest view pixels, against the FP64 oracle on its own dRadon/ds "
+                                                    "of the job's views"},
             "jobs_mix": "detector uniform {256^2, 620x480, 976^2}, views U{50..500}, kappa U{256..1024}, "
                         "FP16 storage, 20 gradient iterations + final evaluation, Poisson arrivals",
             "wall_includes": "admission (H2D of projections from pinned host pools, dRadon/ds precompute) and "
