@@ -72,14 +72,33 @@ def test_grad_matches_oracle(c):
     assert abs(total - ref["total"]) <= H.TOL_F32 * ref["total"]
 
 
+@functools.lru_cache(maxsize=None)
+def _opposed_case():
+    """c4 geometry (opposed views, full-pi arcs, tiles across the alpha fold) on a
+    smaller dRadon/ds grid, with a seeded motion."""
+    views = (0, 1, 310, 619, 620, 621, 930, 1239)
+    sc = H.scan("c4", views)
+    S = orc.radon_derivative(sc["P"], sc["images"], 256, 346)
+    rng = np.random.default_rng(11)
+    th = np.concatenate([rng.normal(0, 0.01, (len(views), 3)), rng.normal(0, 1.0, (len(views), 3))], axis=1)
+    return sc, S, th
+
+
 @pytest.mark.parametrize("dtype_name", ["float16", "bfloat16"])
-def test_grad_reduced_precision_storage(dtype_name):
+@pytest.mark.parametrize("case", ["c3-20views", "c4-opposed-k77"])
+def test_grad_reduced_precision_storage(dtype_name, case):
     """The adjoint reading FP16 (per-view scale) and BF16 sinograms, against the oracle's
     gradient on the stored values themselves (dequantized to FP64): both sides see the
-    same inputs, so the FP32 bar holds."""
+    same inputs, so the FP32 bar holds.  Cases: the 20-view motion subset (K = 512) and
+    opposed full-scan views at K = 77 (fold tiles, the ragged last tile)."""
     import paper_1806_02637_gb300 as ecc
-    cfg, sc, S = _case()
-    th = sc["motion"]
+    if case == "c3-20views":
+        cfg, sc, S = _case()
+        th, K = sc["motion"], cfg.K
+    else:
+        cfg = synth.CONFIGS["c4"]
+        sc, S, th = _opposed_case()
+        K = 77
     if dtype_name == "float16":
         q, scales = H.quantize_f16(S)
         S_dev, sc_dev = torch.from_numpy(q).cuda(), torch.from_numpy(scales).cuda()
@@ -87,11 +106,11 @@ def test_grad_reduced_precision_storage(dtype_name):
     else:
         S_ref = H.round_bf16(S)
         S_dev, sc_dev = torch.from_numpy(S_ref.astype(np.float32)).to(torch.bfloat16).cuda(), None
-    r = ecc.ecc_evaluate_grad(_ctx(), _cuda(sc["P"]), S_dev, cfg.W, cfg.H, cfg.K, motion=_cuda(th), scales=sc_dev)
+    r = ecc.ecc_evaluate_grad(_ctx(), _cuda(sc["P"]), S_dev, cfg.W, cfg.H, K, motion=_cuda(th), scales=sc_dev)
     torch.cuda.synchronize()
-    ref = orc.ecc_grad(sc["P"], S_ref, cfg.W, cfg.H, cfg.K, motion=th)
+    ref = orc.ecc_grad(sc["P"], S_ref, cfg.W, cfg.H, K, motion=th)
     err, comp = grad_errors(r["grad"].cpu().numpy(), ref["grad"])
-    print(f"gradient vs oracle, 20 views, {dtype_name} storage: rel L2 {err:.2e}, max component / norm {comp:.2e}")
+    print(f"gradient vs oracle, {case}, {dtype_name} storage: rel L2 {err:.2e}, max component / norm {comp:.2e}")
     assert err <= TOL_GRAD and comp <= TOL_GRAD, (err, comp)
     assert abs(float(r["total"].cpu()[0]) - ref["total"]) <= H.TOL_F32 * ref["total"]
 
